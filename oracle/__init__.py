@@ -1,0 +1,11 @@
+"""FP64 CPU oracle of the DART-Ray V2 ray-propagation sweep.
+
+Test infrastructure only: tests/, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of bench.py use it.  The CUDA
+library never imports, links or calls anything here.
+"""
+from .oracle import (build, OracleParams, Oracle, pix2vec, vec2pix, hg, k_hp_real, k_hp,
+                     locate, trace, tau_between, LEDGER_NAMES, COUNTER_NAMES)
+
+__all__ = ["build", "OracleParams", "Oracle", "pix2vec", "vec2pix", "hg", "k_hp_real", "k_hp",
+           "locate", "trace", "tau_between", "LEDGER_NAMES", "COUNTER_NAMES"]

@@ -1,0 +1,330 @@
+"""ctypes wrapper of oracle/dartray_oracle.c (test infrastructure only).
+
+The C file is compiled with the host C compiler into oracle/_build/ on first
+use (or by ``build()``).  All arrays handed to the C code are float64 copies
+of the float32 grid inputs, so both sides see the same numbers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dartray_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MAXL = 16
+LEDGER_NAMES = ("emitted", "absorbed", "scattered", "escaped", "blocked", "cut", "skipped")
+COUNTER_NAMES = ("rays", "crossings", "splits", "merges", "blocks", "escapes", "cuts", "lows",
+                 "resumes", "waves", "sources")
+
+
+def build(force=False, openmp=False):
+    """Compile the oracle shared library (plain C, -O2, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    cc = os.environ.get("CC", "gcc")
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = [cc, "-O2", "-std=c11", "-fno-fast-math", "-ffp-contract=off", "-shared", "-fPIC",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Grid(C.Structure):
+    _fields_ = [("nroot", C.c_int32 * 3), ("root_lo", C.c_double * 3), ("root_size", C.c_double),
+                ("n_nodes", C.c_int32), ("n_leaf", C.c_int32), ("n_lambda", C.c_int32),
+                ("first_child", C.c_void_p), ("leaf_of_node", C.c_void_p),
+                ("kappa_rho", C.c_void_p), ("emis", C.c_void_p), ("albedo", C.c_void_p),
+                ("g", C.c_void_p), ("n_point", C.c_int32), ("point_xyz", C.c_void_p),
+                ("point_lum", C.c_void_p)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("a_rt", C.c_double), ("r_pre", C.c_double), ("f_l", C.c_double),
+                ("c_light", C.c_double), ("n_rays_min", C.c_int32), ("n_rays_max", C.c_int32),
+                ("k0", C.c_int32), ("k_ray_max", C.c_int32), ("k_sca_cap", C.c_int32),
+                ("n_fwhm", C.c_int32), ("merge", C.c_int32), ("max_cross", C.c_int32),
+                ("max_waves", C.c_int32), ("src_stride", C.c_int32), ("src_offset", C.c_int32)]
+
+
+class _State(C.Structure):
+    _fields_ = [("k_lam", C.c_int32 * MAXL), ("off_lam", C.c_int64 * MAXL), ("sca_len", C.c_int64),
+                ("U", C.c_void_p), ("U_LL", C.c_void_p), ("pend_a", C.c_void_p),
+                ("pend_b", C.c_void_p), ("cur_is_a", C.c_int32), ("jsca_total", C.c_void_p),
+                ("ledger", (C.c_double * 7) * MAXL), ("counters", C.c_int64 * 11),
+                ("L_sca2", C.c_double), ("f_u", C.c_double), ("n_src", C.c_int32)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.c_void_p
+            lib.or_pix2vec.argtypes = [C.c_int, C.c_int64, P]
+            lib.or_vec2pix.argtypes = [C.c_int, P]
+            lib.or_vec2pix.restype = C.c_int64
+            lib.or_hg.argtypes = [C.c_double, C.c_double]
+            lib.or_hg.restype = C.c_double
+            lib.or_k_hp_real.argtypes = [C.c_double, C.c_int]
+            lib.or_k_hp_real.restype = C.c_double
+            lib.or_k_hp.argtypes = [C.c_double, C.c_int, C.c_int]
+            lib.or_locate.argtypes = [P, P, P, P]
+            lib.or_trace.argtypes = [P, P, P, C.c_double, C.c_int, P, P, P]
+            lib.or_setup.argtypes = [P, P, P]
+            lib.or_setup.restype = C.c_int64
+            lib.or_direct.argtypes = [P, P, P]
+            lib.or_scatter_iter.argtypes = [P, P, P, P]
+            lib.or_run_phase.argtypes = [P, P, P, C.c_int]
+            lib.or_tau.argtypes = [P, C.c_int, P, P]
+            lib.or_tau.restype = C.c_double
+            lib.or_map.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, P]
+            lib.or_pending_next.argtypes = [P]
+            lib.or_pending_next.restype = C.c_void_p
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None and a.size else None
+
+
+# --------------------------------------------------------------- small pure functions
+def pix2vec(k, p):
+    lib = _load()
+    out = np.zeros(3)
+    lib.or_pix2vec(int(k), int(p), _ptr(out))
+    return out
+
+
+def pix2vec_all(k):
+    return np.array([pix2vec(k, p) for p in range(12 * 4 ** k)])
+
+
+def vec2pix(k, v):
+    lib = _load()
+    v = np.ascontiguousarray(v, np.float64)
+    return int(lib.or_vec2pix(int(k), _ptr(v)))
+
+
+def hg(g, mu):
+    return _load().or_hg(float(g), float(mu))
+
+
+def k_hp_real(g, n_fwhm=5):
+    return _load().or_k_hp_real(float(g), int(n_fwhm))
+
+
+def k_hp(g, n_fwhm=5, cap=3):
+    return _load().or_k_hp(float(g), int(n_fwhm), int(cap))
+
+
+# --------------------------------------------------------------- grid
+class _GridHandle:
+    """Keeps the float64 copies alive for as long as the C struct is used."""
+
+    def __init__(self, grid):
+        self.fc = np.ascontiguousarray(grid.first_child, np.int32)
+        self.lon = np.ascontiguousarray(grid.leaf_of_node, np.int32)
+        self.kr = np.ascontiguousarray(grid.kappa_rho, np.float64)
+        self.em = np.ascontiguousarray(grid.emissivity, np.float64)
+        self.al = np.ascontiguousarray(grid.albedo, np.float64)
+        self.g = np.ascontiguousarray(grid.g, np.float64)
+        self.pxyz = np.ascontiguousarray(grid.point_xyz, np.float64).reshape(-1, 3)
+        self.plum = np.ascontiguousarray(grid.point_lum, np.float64).reshape(self.pxyz.shape[0], grid.n_lambda)
+        s = _Grid()
+        s.nroot[:] = grid.nroot
+        s.root_lo[:] = grid.root_lo
+        s.root_size = grid.root_size
+        s.n_nodes = grid.n_nodes
+        s.n_leaf = grid.n_leaf
+        s.n_lambda = grid.n_lambda
+        s.first_child = _ptr(self.fc)
+        s.leaf_of_node = _ptr(self.lon)
+        s.kappa_rho = _ptr(self.kr)
+        s.emis = _ptr(self.em)
+        s.albedo = _ptr(self.al)
+        s.g = _ptr(self.g)
+        s.n_point = self.pxyz.shape[0]
+        s.point_xyz = _ptr(self.pxyz)
+        s.point_lum = _ptr(self.plum)
+        self.s = s
+
+    @property
+    def ref(self):
+        return C.byref(self.s)
+
+
+def locate(grid, p, n):
+    lib = _load()
+    h = grid if isinstance(grid, _GridHandle) else _GridHandle(grid)
+    p = np.ascontiguousarray(p, np.float64)
+    n = np.ascontiguousarray(n, np.float64)
+    box = np.zeros(4)
+    leaf = lib.or_locate(h.ref, _ptr(p), _ptr(n), _ptr(box))
+    return leaf, box
+
+
+def trace(grid, xs, n, d0=0.0, cap=100000):
+    lib = _load()
+    h = grid if isinstance(grid, _GridHandle) else _GridHandle(grid)
+    xs = np.ascontiguousarray(xs, np.float64)
+    n = np.ascontiguousarray(n, np.float64)
+    leaf = np.zeros(cap, np.int32)
+    tin = np.zeros(cap)
+    tout = np.zeros(cap)
+    cnt = lib.or_trace(h.ref, _ptr(xs), _ptr(n), float(d0), int(cap), _ptr(leaf), _ptr(tin), _ptr(tout))
+    if cnt < 0:
+        raise OracleError(_ERRORS.get(cnt, f"error {cnt}"))
+    return leaf[:cnt], tin[:cnt], tout[:cnt]
+
+
+def tau_between(grid, a, b, lam=0):
+    lib = _load()
+    h = grid if isinstance(grid, _GridHandle) else _GridHandle(grid)
+    a = np.ascontiguousarray(a, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    return lib.or_tau(h.ref, int(lam), _ptr(a), _ptr(b))
+
+
+# --------------------------------------------------------------- solver
+@dataclasses.dataclass
+class OracleParams:
+    """Parameters of the sweep (defaults are the readings of the paper's
+    input-defined values used throughout the tests)."""
+    a_rt: float = 0.05
+    r_pre: float = 0.3
+    f_l: float = 0.01
+    c_light: float = 1.0
+    n_rays_min: int = 5
+    n_rays_max: int = 40
+    k0: int = 2
+    k_ray_max: int = 13
+    k_sca_cap: int = 3
+    n_fwhm: int = 5
+    merge: int = 1
+    max_cross: int = 1 << 22
+    max_waves: int = 200
+    src_stride: int = 1
+    src_offset: int = 0
+
+    def to_c(self):
+        p = _Params()
+        for f in dataclasses.fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+_ERRORS = {-1: "out of memory", -2: "crossing cap reached", -3: "wave cap reached",
+           -4: "source cell not found", -5: "no progress across a face (inexact grid coordinates)"}
+
+
+class Oracle:
+    """Stateful FP64 solver mirroring the library calls: direct(),
+    scatter_iter(), rfed(), jsca(), map()."""
+
+    def __init__(self, grid, params: OracleParams | None = None):
+        self.grid = grid
+        self.params = params or OracleParams()
+        self._lib = _load()
+        self._g = _GridHandle(grid)
+        self._p = self.params.to_c()
+        self._s = _State()
+        n = grid.n_leaf * grid.n_lambda
+        self.U = np.zeros(n)
+        self.U_LL = np.zeros(n)
+        sca_len = self._lib.or_setup(self._g.ref, C.byref(self._p), C.byref(self._s))
+        self.pend_a = np.zeros(sca_len)
+        self.pend_b = np.zeros(sca_len)
+        self.jsca_total = np.zeros(sca_len)
+        s = self._s
+        s.U, s.U_LL = _ptr(self.U), _ptr(self.U_LL)
+        s.pend_a, s.pend_b = self.pend_a.ctypes.data, self.pend_b.ctypes.data
+        s.jsca_total = self.jsca_total.ctypes.data
+        self.k_lam = [s.k_lam[l] for l in range(grid.n_lambda)]
+        self.off_lam = [s.off_lam[l] for l in range(grid.n_lambda)]
+
+    def _check(self, rc):
+        if rc:
+            raise OracleError(_ERRORS.get(rc, f"error {rc}"))
+
+    def reset_stats(self):
+        for l in range(MAXL):
+            for i in range(7):
+                self._s.ledger[l][i] = 0.0
+        for i in range(11):
+            self._s.counters[i] = 0
+
+    def stats(self):
+        nl = self.grid.n_lambda
+        led = {name: np.array([self._s.ledger[l][i] for l in range(nl)])
+               for i, name in enumerate(LEDGER_NAMES)}
+        cnt = {name: int(self._s.counters[i]) for i, name in enumerate(COUNTER_NAMES)}
+        return led, cnt
+
+    def direct(self):
+        self._check(self._lib.or_direct(self._g.ref, C.byref(self._p), C.byref(self._s)))
+
+    def run_phase(self, mode):
+        self._check(self._lib.or_run_phase(self._g.ref, C.byref(self._p), C.byref(self._s), int(mode)))
+
+    def scatter_iter(self):
+        rem = C.c_double(0)
+        self._check(self._lib.or_scatter_iter(self._g.ref, C.byref(self._p), C.byref(self._s),
+                                              C.byref(rem)))
+        return rem.value
+
+    @property
+    def f_u(self):
+        return self._s.f_u
+
+    @property
+    def n_src(self):
+        return self._s.n_src
+
+    @property
+    def L_sca2(self):
+        return self._s.L_sca2
+
+    def rfed(self):
+        """U [n_leaf, n_lambda] and absorbed luminosity L_abs = (1-albedo)
+        kappa*rho c V U per leaf."""
+        g = self.grid
+        U = self.U.reshape(g.n_leaf, g.n_lambda).copy()
+        V = g.leaf_size ** 3
+        L_abs = (1.0 - g.albedo.astype(np.float64))[None, :] * g.kappa_rho.astype(np.float64) \
+            * self.params.c_light * V[:, None] * U
+        return U, L_abs
+
+    def pending_next(self):
+        ptr = self._lib.or_pending_next(C.byref(self._s))
+        return self.pend_a if ptr == self.pend_a.ctypes.data else self.pend_b
+
+    def jsca(self, l=0, which="total"):
+        g = self.grid
+        npx = 12 * 4 ** self.k_lam[l]
+        src = self.jsca_total if which == "total" else self.pending_next()
+        return src[self.off_lam[l]: self.off_lam[l] + g.n_leaf * npx].reshape(g.n_leaf, npx)
+
+    def map(self, observer, nside_k, max_sub=4, use_jsca=True):
+        g = self.grid
+        out = np.zeros(g.n_lambda * 12 * 4 ** nside_k)
+        obs = np.ascontiguousarray(observer, np.float64)
+        self._check(self._lib.or_map(self._g.ref, C.byref(self._s), _ptr(obs), int(nside_k),
+                                     int(max_sub), int(bool(use_jsca)), _ptr(out)))
+        return out.reshape(g.n_lambda, -1)
