@@ -1,0 +1,286 @@
+"""Benchmark of the ray-propagation sweep on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path over the exponential-disk galaxy
+(297,840 adaptive leaves, B band, albedo 0.6, g = 0.6, a_RT = 0.05): step 1
+(U_LL within R_pre), step 2 (direct light with ray blocking), scattering
+iterations until the pending scattered luminosity is below f_L = 1% of the
+step-2 total (at most 12), and an internal-observer HEALPix map
+(nside 64, observer at R = 8 kpc in the mid-plane).  The grid is resident in
+HBM before the timed region; every step restarts the sweep from scratch.
+
+Metric: ray-cell crossings per second (crossings of steps 1-3 over the step
+time).  Also reported: seconds per scattering iteration.  The L2 cache is
+flushed (a 512 MB write) between timed steps.
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on
+the host cores on a bounded sample of the same workload (every 400th source).
+With N > 1 GPUs each rank runs an independent replica (the path has no
+exchange step on one GPU); the value is the sum over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "galaxy disk + bulge, 297840 adaptive leaves (9x9x1 roots of 4 kpc, 6 levels), 1 lambda"
+PARAMS = dict(a_rt=0.05, n_rays_min=5, n_rays_max=40, k0=2, merge=1)
+F_L = 0.01
+MAX_ITERS = 12
+OBSERVER = (8.0, 0.0, 0.0)
+MAP_K = 6  # nside 64
+MAP_SUB = 3
+HBM_FALLBACK_GBS = 6800.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", HBM_FALLBACK_GBS)), "of measured"
+    return HBM_FALLBACK_GBS, "of fallback"
+
+
+def bytes_per_crossing(nl):
+    """Algorithmic bytes of one crossing (leaf box 16 B + 6 face links 24 B +
+    node child word 4 B, kappa*rho 4 B and U_LL 4 B per wavelength, U
+    read-modify-write 8 B per wavelength); the j_sca row update adds 8 B per
+    pixel updated (counted separately)."""
+    return 44 + 16 * nl
+
+
+def make_workload():
+    import synth
+    grid = synth.config2()
+    r_pre = 0.15 * grid.model_size
+    return grid, dict(PARAMS, r_pre=r_pre)
+
+
+class Clocks:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, gpu_index=0):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except OSError:
+            return None
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        rows = [r for r in rows if r[0] == str(gpu_index)] or rows
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def run_step(gpu, grid):
+    st = gpu.direct()
+    cross = st["crossings"]
+    march_ms = st["march_ms"]
+    march_cross = st["crossings"]
+    jpix = st["jsca_pixels"]
+    launches = st["kernel_launches"]
+    it_ms = []
+    it = 0
+    while it < MAX_ITERS:
+        rem, s2 = gpu.scatter_iter()
+        it += 1
+        cross += s2["crossings"]
+        march_ms += s2["march_ms"]
+        march_cross += s2["crossings"]
+        jpix += s2["jsca_pixels"]
+        launches += s2["kernel_launches"]
+        it_ms.append(s2["gpu_ms"])
+        if rem < F_L:
+            break
+    m = gpu.map(OBSERVER, MAP_K, max_sub=MAP_SUB, use_jsca=True)
+    launches += 1
+    return dict(crossings=cross, march_ms=march_ms, march_crossings=march_cross, jsca_pixels=jpix,
+                iters=it, iter_ms=it_ms, launches=launches, map_sum=float(m.sum()))
+
+
+def cpu_sample(grid, params, stride):
+    import oracle
+    p = oracle.OracleParams(**{k: v for k, v in params.items() if k in oracle.OracleParams.__dataclass_fields__},
+                            src_stride=stride)
+    o = oracle.Oracle(grid, p)
+    t0 = time.perf_counter()
+    o.direct()
+    c = o.stats()[1]["crossings"]
+    o.scatter_iter()
+    c += o.stats()[1]["crossings"]
+    dt = time.perf_counter() - t0
+    return c, dt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-stride", type=int, default=400)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    grid, params = make_workload()
+    metric = "ray-cell crossings/s"
+    unit = "crossings/s"
+    config = {"workload": WORKLOAD, "n_leaf": grid.n_leaf, "a_rt": params["a_rt"], "f_l": F_L,
+              "map": f"nside 64 at {OBSERVER} kpc", "l2": "flushed between steps (512 MB write)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        vals, tot_c, tot_t = [], 0, 0.0
+        for s in range(args.warmup + args.steps):
+            c, dt = cpu_sample(grid, params, args.cpu_stride)
+            if s >= args.warmup:
+                vals.append(c / dt)
+                tot_c += c
+                tot_t += dt
+        v = tot_c / tot_t
+        sample = f"every {args.cpu_stride}th source, steps 1-2 + one scattering iteration"
+        print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": unit, "n_gpus": 0,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+                          "higher_is_better": True, "dtype": "f64", "data": "synthetic", "config": config,
+                          "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+                          "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1709_03802_gb300 import DartRay
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    gpu = DartRay(grid, profile=1, **params)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        run_step(gpu, grid)
+    torch.cuda.synchronize()
+    results = []
+    total_ms = 0.0
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    with clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = run_step(gpu, grid)
+            e1.record()
+            torch.cuda.synchronize()
+            barrier()
+            total_ms += e0.elapsed_time(e1)
+            results.append(r)
+    clocks = clk.summary(local_rank)
+    ms = total_ms / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cross = float(np.mean([r["crossings"] for r in results]))
+    value = cross * world / (ms / 1e3)
+    it_ms = [x for r in results for x in r["iter_ms"]]
+    march_ms = sum(r["march_ms"] for r in results)
+    nl = grid.n_lambda
+    alg_bytes = sum(r["march_crossings"] * bytes_per_crossing(nl) + 8 * r["jsca_pixels"] for r in results)
+    peak, peak_src = peaks()
+    achieved = alg_bytes / (march_ms / 1e3) / 1e9 if march_ms > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "march_kernel<1,SCATTER/DIRECT/LL>", "peak_source": peak_src,
+                "march_share_of_step": march_ms / total_ms if total_ms else None}
+
+    # end-to-end through the C ABI with host buffers: create (H2D of the
+    # inputs), sweep, U / L_abs / map back to host
+    e2e = None
+    if rank == 0:
+        t0 = time.perf_counter()
+        g2 = DartRay(grid, **params)
+        r2 = run_step(g2, grid)
+        U, L = g2.rfed()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        h2d = sum(np.asarray(a).nbytes for a in (grid.first_child, grid.leaf_of_node, grid.kappa_rho,
+                                                 grid.emissivity, grid.albedo, grid.g))
+        d2h = U.nbytes + L.nbytes + 4 * nl * 12 * 4 ** MAP_K
+        e2e = {"value": r2["crossings"] / dt, "unit": unit, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "seconds": dt}
+        g2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        c, dt = cpu_sample(grid, params, args.cpu_stride)
+        cpu = {"value": c / dt, "unit": unit, "cores": 1, "kind": "oracle",
+               "sample": f"every {args.cpu_stride}th source, steps 1-2 + one scattering iteration, "
+                         f"{c} crossings in {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+                "s_per_scatter_iter": float(np.mean(it_ms)) / 1e3 if it_ms else None,
+                "scatter_iters_per_step": float(np.mean([r["iters"] for r in results])),
+                "crossings_per_step": cross,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(sum(r["launches"] for r in results)), "clocks": clocks}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

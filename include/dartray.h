@@ -1,0 +1,213 @@
+/*
+ * dartray.h -- C ABI of the GB300 ray-propagation sweep of DART-Ray V2
+ * (Natale et al. 2017, "Ray-tracing 3D dust radiative transfer with DART-Ray:
+ * code upgrade and public release").
+ *
+ * The library solves, on one GPU, the three-step radiative-transfer sweep of
+ * the paper's Sect. 2 for the stellar emission of a model on an adaptive 3D
+ * Cartesian grid: the lower limit U_LL of the radiation-field energy density
+ * (RFED), the direct light with ray blocking (Eq. 1), and the scattering
+ * iterations; and it projects the result onto HEALPix maps for an observer
+ * inside the model.  Rays follow HEALPix directions (Sect. 3.1.1) and are
+ * split (Eq. 2) or merged (Eq. 3) as they propagate; the scattering source
+ * function is sampled on HEALPix(k_lambda) (Sect. 3.1.2, Eq. 4, Eq. 5); the
+ * blocking threshold is f_U = 4 a_RT / N_s (Sect. 3.5, Eq. 10).
+ *
+ * Conventions shared by every call
+ *   - Return value: DARTRAY_OK (0) or a negative DARTRAY_E_* code.  A failed
+ *     call leaves a message readable with dartray_last_error() (thread-local).
+ *     No call aborts the process; device-side failures (crossing cap, queue
+ *     overflow) are reported through a device status word read by the host.
+ *   - Units: lengths, kappa*rho (1/length), emissivity (luminosity per volume
+ *     per steradian) and c_light are in the caller's model units.  U is
+ *     returned in luminosity / (length^3 * c_light units).
+ *   - Arrays are dense, row-major, float32 unless stated.  Pointers marked
+ *     "host or device" are device pointers when the flag next to them is 1.
+ *   - Streams: all device work of a grid is issued on the cudaStream_t given
+ *     to dartray_grid_create; calls synchronise that stream before returning.
+ *   - Thread safety: one grid must not be used by two threads at once.
+ */
+#ifndef DARTRAY_H
+#define DARTRAY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DARTRAY_MAX_LAMBDA 16
+
+enum {
+    DARTRAY_OK = 0,
+    DARTRAY_E_INVAL = -1,   /* invalid argument or grid description */
+    DARTRAY_E_NOMEM = -2,   /* device or host allocation failed */
+    DARTRAY_E_CUDA = -3,    /* CUDA runtime error */
+    DARTRAY_E_QUEUE = -4,   /* ray queues too small even for one source */
+    DARTRAY_E_LIMIT = -5,   /* crossing cap per ray or wave cap reached */
+    DARTRAY_E_STATE = -6    /* call out of order (e.g. scatter before direct) */
+};
+
+typedef struct dartray_grid dartray_grid; /* opaque, owned by the library */
+
+/*
+ * Model description (Sect. 2: "an adaptive 3D Cartesian grid of cells, each
+ * with a given input value of stellar volume emissivity and dust optical
+ * depth per unit length"; albedo and HG g per wavelength from the dust model;
+ * point sources of Sect. 3.6.1).
+ *
+ * Layout: a lattice of nroot[0] x nroot[1] x nroot[2] cubic root cells of side
+ * root_size, lower corner root_lo.  Each root tops an octree.  Nodes
+ * 0 .. nroot[0]*nroot[1]*nroot[2]-1 are the roots (x fastest, then y, then
+ * z).  A refined node's 8 children are contiguous from first_child[node], in
+ * the order bx + 2*by + 4*bz (b = 1: upper half on that axis).  Leaves have
+ * first_child = -1 and a leaf id leaf_of_node[node] in [0, n_leaf); internal
+ * nodes have leaf_of_node = -1.  All face coordinates of all nodes must be
+ * exactly representable in float32 (dyadic grids); otherwise
+ * DARTRAY_E_INVAL.
+ *
+ * Ownership: caller-owned; copied into device memory by dartray_grid_create,
+ * not referenced afterwards.
+ */
+typedef struct dartray_grid_desc {
+    int32_t nroot[3];
+    double root_lo[3];
+    double root_size;
+    int32_t n_nodes, n_leaf, n_lambda;   /* 1 <= n_lambda <= DARTRAY_MAX_LAMBDA */
+    const int32_t *first_child;          /* [n_nodes] host or device */
+    const int32_t *leaf_of_node;         /* [n_nodes] host or device */
+    const float *kappa_rho;              /* [n_leaf][n_lambda] extinction per length, >= 0 */
+    const float *emissivity;             /* [n_leaf][n_lambda] luminosity/volume/sr, >= 0 */
+    const float *albedo;                 /* [n_lambda] in [0, 1] */
+    const float *g;                      /* [n_lambda] HG anisotropy in (-1, 1) */
+    int32_t n_point;                     /* point sources (may be 0) */
+    const float *point_xyz;              /* [n_point][3] positions inside the model */
+    const float *point_lum;              /* [n_point][n_lambda] total luminosity */
+    int32_t inputs_on_device;            /* 1: every pointer above is a device pointer */
+} dartray_grid_desc;
+
+/*
+ * Algorithm parameters.  The paper leaves most of them input-defined
+ * (N_rays and N_rays^max of Eq. 2-3, R_pre of Sect. 2, n_FWHM and the cap on
+ * k_lambda,HP of Sect. 3.1.2, a_RT of Sect. 3.5, f_L of Sect. 2).
+ * dartray_params_default() fills the defaults listed beside each field.
+ */
+typedef struct dartray_params {
+    double a_rt;          /* accuracy parameter; f_U = 4 a_rt / N_s (0.05) */
+    double r_pre;         /* step-1 radius R_pre, model length units (0.15 * model size) */
+    double f_l;           /* scattering stop fraction f_L (0.01), used by callers */
+    double c_light;       /* light speed (1) */
+    int32_t n_rays_min;   /* N_rays of Eq. 2 (5) */
+    int32_t n_rays_max;   /* N_rays^max of Eq. 3 (40) */
+    int32_t k0;           /* initial ray HEALPix level (2) */
+    int32_t k_ray_max;    /* highest ray level, <= 13 (13) */
+    int32_t k_sca_cap;    /* cap on k_lambda,HP, <= 3 (3) */
+    int32_t n_fwhm;       /* n_FWHM (5) */
+    int32_t merge;        /* 1: merge rays by Eq. 3 (1) */
+    int32_t max_cross;    /* crossings per ray before DARTRAY_E_LIMIT (1 << 22) */
+    int32_t max_waves;    /* waves per source batch before DARTRAY_E_LIMIT (200) */
+    int32_t src_stride;   /* process sources s with s % src_stride == src_offset (1) */
+    int32_t src_offset;   /* (0) */
+    int64_t queue_rays;   /* capacity of each ray queue, records (1 << 24) */
+    int64_t src_batch;    /* sources traced together; 0 = all (0) */
+    int32_t profile;      /* 1: time every ray-march launch with CUDA events (0) */
+    int32_t reserved;
+} dartray_params;
+
+/* Per-call statistics.  Ledger entries are luminosities per wavelength of the
+ * last phase of the call (emitted = absorbed + scattered + escaped + blocked
+ * + cut + skipped to rounding); counters cover the whole call. */
+typedef struct dartray_stats {
+    int64_t rays, crossings, splits, merges, blocks, escapes, cuts, lows, resumes, waves,
+        sources;
+    double emitted[DARTRAY_MAX_LAMBDA];
+    double absorbed[DARTRAY_MAX_LAMBDA];
+    double scattered[DARTRAY_MAX_LAMBDA];
+    double escaped[DARTRAY_MAX_LAMBDA];
+    double blocked[DARTRAY_MAX_LAMBDA];
+    double cut[DARTRAY_MAX_LAMBDA];
+    double skipped[DARTRAY_MAX_LAMBDA];
+    double f_u;           /* f_U of the last phase (Eq. 10) */
+    double l_sca2;        /* total scattered luminosity at the end of step 2 */
+    double gpu_ms;        /* device time of the call (CUDA events) */
+    int64_t kernel_launches; /* kernels launched by the call */
+    double march_ms;      /* with params.profile: summed ray-march kernel time */
+    int64_t march_launches; /* ray-march kernel launches of the call */
+    int64_t jsca_pixels;  /* scattering source-function pixels updated */
+} dartray_stats;
+
+/* Fill *p with the defaults above (r_pre is set when the grid is created if
+ * left negative). */
+int dartray_params_default(dartray_params *p);
+
+/*
+ * Validate the description, build the leaf face links (ropes) and upload the
+ * grid to the current CUDA device; allocate U, U_LL, the two pending j_sca
+ * buffers, the total j_sca and the ray queues.  k_lambda,HP per wavelength
+ * follows Eq. 5 (integer part, clamped to [0, k_sca_cap]).  cuda_stream is a
+ * cudaStream_t (NULL = default stream).  On success *out owns all device
+ * memory until dartray_grid_destroy.  Errors: INVAL (bad tree, non-dyadic
+ * coordinates, bad sizes), NOMEM, CUDA.
+ */
+int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *params,
+                        void *cuda_stream, dartray_grid **out);
+
+/* Steps 1 and 2 of Sect. 2: U_LL within R_pre, then direct light with ray
+ * blocking (Eq. 1), depositing U, and the scattered luminosity into the
+ * pending j_sca buffer; afterwards U_LL <- U and j_sca_total += pending.
+ * stats may be NULL.  Errors: LIMIT, QUEUE, CUDA. */
+int dartray_direct(dartray_grid *grid, dartray_stats *stats);
+
+/* One scattering iteration (Sect. 2): the pending scattered luminosity of the
+ * previous phase is emitted from every dusty cell along HEALPix directions
+ * (per-sr luminosity = pending pixel / pixel solid angle), depositing U and a
+ * new pending buffer; afterwards U_LL <- U and j_sca_total += pending.
+ * *remaining_frac = (pending luminosity) / (scattered luminosity at the end of
+ * step 2); callers stop once it is below f_L.  Errors: STATE (no dartray_direct
+ * yet), LIMIT, QUEUE, CUDA. */
+int dartray_scatter_iter(dartray_grid *grid, double *remaining_frac, dartray_stats *stats);
+
+/* RFED U [n_leaf][n_lambda] and absorbed luminosity
+ * L_abs = (1 - albedo) * kappa_rho * c_light * V * U [n_leaf][n_lambda]
+ * (either pointer may be NULL), written to host or device memory. */
+int dartray_rfed(dartray_grid *grid, float *U, float *L_abs, int dst_is_device);
+
+/* j_sca layout: k_lambda per wavelength, offset of each wavelength block and
+ * total length; block l is [n_leaf][12 * 4^k_lambda[l]] (nested pixels). */
+int dartray_jsca_layout(const dartray_grid *grid, int32_t *k_lambda, int64_t *offsets,
+                        int64_t *total_len);
+
+/* Copy j_sca: which = 0 total scattered luminosity per pixel (all phases so
+ * far), 1 = pending (deposited by the last phase).  out has total_len floats. */
+int dartray_jsca(dartray_grid *grid, int which, float *out, int dst_is_device);
+
+/*
+ * Surface-brightness map for an observer inside the model (Sect. 2 end,
+ * Sect. 3.6.3): I_obs = I_0 exp(-tau).  Every leaf is projected as a point at
+ * its centre, subdivided into octants (at most max_sub times) while it
+ * subtends more than one map pixel or contains the observer; I_0 is the
+ * (sub)cell's per-sr luminosity toward the observer (j V plus the total j_sca
+ * pixel that holds that direction over its solid angle), tau the optical
+ * depth from the (sub)cell centre to the observer.  map[l][p] (nested
+ * HEALPix, level nside_k, 12*4^nside_k pixels) receives
+ * sum I_0 exp(-tau) / (r^2 Omega_pix).  use_jsca = 0 maps the stellar light
+ * only.  Errors: INVAL, CUDA.
+ */
+int dartray_map(dartray_grid *grid, const double observer[3], int32_t nside_k, int32_t max_sub,
+                int32_t use_jsca, float *map, int dst_is_device);
+
+/* Save / restore the RFED and source-function state (U, U_LL, pending,
+ * j_sca_total and the step-2 scattered luminosity) to a raw binary file, so
+ * that maps can be made without repeating the sweep. */
+int dartray_state_save(dartray_grid *grid, const char *path);
+int dartray_state_load(dartray_grid *grid, const char *path);
+
+void dartray_grid_destroy(dartray_grid *grid);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *dartray_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DARTRAY_H */

@@ -322,8 +322,17 @@ static double or_exit(const double xs[3], const double n[3], const double box[4]
     }
     int m = 0;
     for (int a = 0; a < 3; ++a) {
-        if (t[a] == tmin) { m |= 1 << a; pe[a] = bnd[a]; }
-        else pe[a] = xs[a] + tmin * n[a];
+        if (t[a] == tmin) {
+            m |= 1 << a;
+            pe[a] = bnd[a];
+        } else {
+            /* the exit point lies on the closed box; rounding must not move it
+             * outside (that could send the ray back into a cell behind it) */
+            double v = xs[a] + tmin * n[a];
+            if (v < box[a]) v = box[a];
+            if (v > box[a] + box[3]) v = box[a] + box[3];
+            pe[a] = v;
+        }
     }
     *tie = m;
     return tmin;
@@ -434,12 +443,34 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
 
     double box[4];
     int leaf;
+    int start_axis = -1;      /* face the ray starts on, if any */
+    double start_coord = 0;
     if (ray->hint_leaf >= 0) {
         leaf = ray->hint_leaf;
         memcpy(box, ray->hint_box, sizeof box);
     } else {
         double p[3] = {C->xs[0] + ray->d * n[0], C->xs[1] + ray->d * n[1], C->xs[2] + ray->d * n[2]};
+        /* Children restart at the parent's distance d_ray (Sect. 3.1.1).  A
+         * child whose direction has the same component as its parent along
+         * the axis of the face the parent entered its last cell through lies,
+         * in exact arithmetic, on that face at distance d_ray; the start point
+         * is taken exactly there (reading: exact evaluation of the rule, so
+         * that rounding does not decide the side of the face). */
+        if (ray->kind == RK_CHILD && ray->plane_axis >= 0) {
+            double np_[3];
+            or_pix2vec(ray->lev - 1, ray->pix >> 2, np_);
+            const int a = ray->plane_axis;
+            if (n[a] == np_[a]) {
+                p[a] = ray->plane_coord;
+                start_axis = a;
+                start_coord = ray->plane_coord;
+            }
+        }
         leaf = or_locate(G, p, n, box);
+    }
+    if (ray->kind == RK_RESUMED) {  /* resumes on the face it stopped at */
+        start_axis = ray->plane_axis;
+        start_coord = ray->plane_coord;
     }
     S->counters[CT_RAYS]++;
     /* HG normalisation for this ray direction (reading: rows normalised so
@@ -462,8 +493,8 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
     }
     double d = ray->d;
     int first = 1;
-    int entry_axis = -1;
-    double entry_coord = 0;
+    int entry_axis = start_axis;  /* face through which the current cell was entered */
+    double entry_coord = start_coord;
     int64_t ncross = 0;
     for (;;) {
         if (++ncross > P->max_cross) return -2;
@@ -519,6 +550,8 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
                 split_c * r2 > beam_units * L * L) {
                 or_ray h = *ray;
                 h.d = d;
+                h.plane_axis = entry_axis;
+                h.plane_coord = entry_coord;
                 if (or_push(high, &h)) return -1;
                 S->counters[CT_SPLIT]++;
                 return 0;

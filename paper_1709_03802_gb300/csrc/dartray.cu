@@ -1,0 +1,834 @@
+// C ABI of the sweep (include/dartray.h): grid creation, the phase driver
+// (step 1 U_LL, step 2 direct light, scattering iterations; Sect. 2 of the
+// paper), read-back, maps and state files.  All device work runs in the
+// kernels of sweep_kernels.cuh and map_kernels.cuh; the host only sequences
+// launches and moves small counters.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dartray.h"
+#include "grid_host.h"
+#include "map_kernels.cuh"
+#include "sweep_kernels.cuh"
+
+using namespace dartray;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail(e_ == cudaErrorMemoryAllocation ? DARTRAY_E_NOMEM : DARTRAY_E_CUDA,            \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+int k_hp_host(double g, int n_fwhm, int cap) {
+    // Eq. 5: k = 0.5 log2(4 pi / (12 theta_min^2)), theta_min = FWHM/n_FWHM of
+    // Phi - Phi(pi); integer part clamped to [0, cap]
+    const double ga = std::fabs(g);
+    if (ga < 1e-12) return 0;
+    const double m = 0.5 * (std::pow(1.0 - ga, -3.0) + std::pow(1.0 + ga, -3.0));
+    const double x = std::pow(m, -2.0 / 3.0);
+    double mu = (1.0 + ga * ga - x) / (2.0 * ga);
+    mu = std::min(1.0, std::max(-1.0, mu));
+    const double th = 2.0 * std::acos(mu) / n_fwhm;
+    const double kr = 0.5 * std::log2(4.0 * kPi / (12.0 * th * th));
+    int k = kr < 0 ? 0 : static_cast<int>(std::floor(kr));
+    return std::min(k, cap);
+}
+
+}  // namespace
+
+struct dartray_grid {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    dartray_params P{};
+    int nl = 0, n_leaf = 0, n_nodes = 0, n_point = 0;
+    DevGrid G{};
+    HostTopo topo;
+    // device arrays
+    int32_t *d_node_child = nullptr, *d_rope = nullptr;
+    float4 *d_node_box = nullptr, *d_leaf_box = nullptr, *d_dirtab = nullptr;
+    float *d_kr = nullptr, *d_emis = nullptr, *d_pxyz = nullptr, *d_plum = nullptr;
+    float *d_U = nullptr, *d_ULL = nullptr, *d_pend[2] = {nullptr, nullptr}, *d_jtot = nullptr;
+    int cur = 0;  // d_pend[cur]: luminosity to emit; d_pend[1-cur]: deposit target
+    long long sca_len = 0;
+    int k_lam[kMaxLambda] = {0};
+    long long off_lam[kMaxLambda] = {0};
+    // sources
+    int *d_flags = nullptr, *d_blocksum = nullptr, *d_total = nullptr, *d_src_idx = nullptr;
+    int *d_src_leaf = nullptr, *d_src_hint = nullptr;
+    float4 *d_src_pos = nullptr;
+    float *d_src_S = nullptr;
+    // queues
+    RayRec *d_H[2] = {nullptr, nullptr}, *d_M[2] = {nullptr, nullptr}, *d_L = nullptr;
+    float *d_HI[2] = {nullptr, nullptr}, *d_MI[2] = {nullptr, nullptr}, *d_LI = nullptr;
+    long long cap = 0;
+    unsigned long long *d_hkey = nullptr;
+    int *d_hcnt = nullptr;
+    int4 *d_hmem = nullptr;
+    long long hcap = 0;
+    WaveCounters *d_wc = nullptr;
+    DevStats *d_st = nullptr;
+    double *d_sum = nullptr;
+    double l_sca2 = 0.0;
+    bool have_direct = false;
+    long long launches = 0;
+    int num_sms = 1;
+    int march_blocks = 1;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t mev0 = nullptr, mev1 = nullptr;  // around each march launch (profile mode)
+    double march_ms = 0.0;
+    long long march_launches = 0;
+};
+
+namespace {
+
+void free_all(dartray_grid *g) {
+    void *ptrs[] = {g->d_node_child, g->d_rope, g->d_node_box, g->d_leaf_box, g->d_dirtab, g->d_kr, g->d_emis,
+                    g->d_pxyz, g->d_plum, g->d_U, g->d_ULL, g->d_pend[0], g->d_pend[1], g->d_jtot, g->d_flags,
+                    g->d_blocksum, g->d_total, g->d_src_idx, g->d_src_leaf, g->d_src_hint, g->d_src_pos,
+                    g->d_src_S, g->d_H[0], g->d_H[1], g->d_M[0], g->d_M[1], g->d_L, g->d_HI[0], g->d_HI[1],
+                    g->d_MI[0], g->d_MI[1], g->d_LI, g->d_hkey, g->d_hcnt, g->d_hmem, g->d_wc, g->d_st, g->d_sum};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    if (g->mev0) cudaEventDestroy(g->mev0);
+    if (g->mev1) cudaEventDestroy(g->mev1);
+}
+
+template <class T>
+int copy_in(T *dst, const T *src, size_t count, bool on_device, cudaStream_t s) {
+    if (count == 0) return DARTRAY_OK;
+    if (!src) return fail(DARTRAY_E_INVAL, "missing input array");
+    CK(cudaMemcpyAsync(dst, src, count * sizeof(T), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return DARTRAY_OK;
+}
+
+template <class T>
+int fetch_host(std::vector<T> &dst, const T *src, size_t count, bool on_device) {
+    dst.resize(count);
+    if (count == 0) return DARTRAY_OK;
+    if (!src) return fail(DARTRAY_E_INVAL, "missing input array");
+    if (on_device) {
+        CK(cudaMemcpy(dst.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(dst.data(), src, count * sizeof(T));
+    }
+    return DARTRAY_OK;
+}
+
+int occupancy_blocks(const void *kernel, int num_sms) {
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+    return std::max(1, per_sm) * num_sms;
+}
+
+template <int NL>
+int launch_march_nl(dartray_grid *g, int mode, const MarchArgs &A) {
+    const int blocks = g->march_blocks;
+    if (mode == MODE_LL) march_kernel<NL, MODE_LL><<<blocks, kBlock, 0, g->stream>>>(g->G, A);
+    else if (mode == MODE_DIRECT) march_kernel<NL, MODE_DIRECT><<<blocks, kBlock, 0, g->stream>>>(g->G, A);
+    else march_kernel<NL, MODE_SCATTER><<<blocks, kBlock, 0, g->stream>>>(g->G, A);
+    ++g->launches;
+    CK(cudaGetLastError());
+    return DARTRAY_OK;
+}
+
+int launch_march(dartray_grid *g, int mode, const MarchArgs &A) {
+    switch (g->nl) {
+    case 1: return launch_march_nl<1>(g, mode, A);
+    case 2: return launch_march_nl<2>(g, mode, A);
+    case 4: return launch_march_nl<4>(g, mode, A);
+    case 8: return launch_march_nl<8>(g, mode, A);
+    case 16: return launch_march_nl<16>(g, mode, A);
+    default: return fail(DARTRAY_E_INVAL, "n_lambda must be 1, 2, 4, 8 or 16");
+    }
+}
+
+// Compacted source table of a phase; returns the count in *n_src.
+int build_sources(dartray_grid *g, int mode, const float *pend_src, int *n_src) {
+    const int n_all = mode == MODE_SCATTER ? g->n_leaf : g->n_leaf + g->n_point;
+    const int nb = (n_all + kBlock - 1) / kBlock;
+    source_flags_kernel<<<nb, kBlock, 0, g->stream>>>(g->G, mode, pend_src, g->P.src_stride, g->P.src_offset,
+                                                      g->d_flags);
+    scan_blocks_kernel<<<nb, kBlock, 0, g->stream>>>(g->d_flags, n_all, g->d_blocksum);
+    scan_offsets_kernel<<<1, 1, 0, g->stream>>>(g->d_blocksum, nb, g->d_total);
+    scatter_compact_kernel<<<nb, kBlock, 0, g->stream>>>(g->d_flags, n_all, g->d_blocksum, g->d_src_idx);
+    g->launches += 4;
+    CK(cudaGetLastError());
+    int total = 0;
+    CK(cudaMemcpyAsync(&total, g->d_total, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (total > 0) {
+        source_table_kernel<<<(total + kBlock - 1) / kBlock, kBlock, 0, g->stream>>>(
+            g->G, mode, g->d_src_idx, total, g->d_src_leaf, g->d_src_hint, g->d_src_pos, g->d_src_S);
+        ++g->launches;
+        CK(cudaGetLastError());
+    }
+    *n_src = total;
+    return DARTRAY_OK;
+}
+
+// Waves of one batch of sources [src_lo, src_lo + nb_src).
+int run_batch(dartray_grid *g, int mode, MarchArgs base, int src_lo, int nb_src, int kstart, int *status,
+              long long *waves) {
+    long long nA = static_cast<long long>(nb_src) * (12ll << (2 * kstart));
+    long long nB = 0;
+    int wave_kind = 0, par = 0;
+    WaveCounters wc{};
+    for (int w = 0;; ++w) {
+        if (nA + nB == 0) break;
+        if (w >= g->P.max_waves) return fail(DARTRAY_E_LIMIT, "wave cap reached");
+        CK(cudaMemsetAsync(g->d_wc, 0, sizeof(WaveCounters), g->stream));
+        MarchArgs A = base;
+        A.wave_kind = wave_kind;
+        A.nA = nA;
+        A.nB = nB;
+        A.H_in = g->d_H[par];
+        A.H_in_I = g->d_HI[par];
+        A.M_in = g->d_M[par];
+        A.M_in_I = g->d_MI[par];
+        A.kstart = kstart;
+        A.src_lo = src_lo;
+        A.H_out = g->d_H[1 - par];
+        A.H_out_I = g->d_HI[1 - par];
+        A.L_out = g->d_L;
+        A.L_out_I = g->d_LI;
+        if (g->P.profile) CK(cudaEventRecord(g->mev0, g->stream));
+        int rc = launch_march(g, mode, A);
+        if (rc) return rc;
+        if (g->P.profile) CK(cudaEventRecord(g->mev1, g->stream));
+        ++g->march_launches;
+        CK(cudaMemcpyAsync(&wc, g->d_wc, sizeof(WaveCounters), cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        if (g->P.profile) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, g->mev0, g->mev1));
+            g->march_ms += ms;
+        }
+        if (wc.status & ST_QUEUE) { *status = ST_QUEUE; return DARTRAY_OK; }
+        if (wc.status & ST_CROSS_CAP) {
+            char m[256];
+            std::snprintf(m, sizeof m,
+                          "crossing cap per ray reached (mode %d, source %d, level %d, pixel %llu, kind %d, "
+                          "leaf %d, d %.9g, side %.9g)",
+                          mode, wc.dbg_src, wc.dbg_lev, static_cast<unsigned long long>(wc.dbg_pix), wc.dbg_kind,
+                          wc.dbg_leaf, static_cast<double>(wc.dbg_d), static_cast<double>(wc.dbg_te));
+            return fail(DARTRAY_E_LIMIT, m);
+        }
+        if (wc.status & ST_NOPROGRESS) return fail(DARTRAY_E_LIMIT, "ray made no progress across a face");
+        DevStats *st = g->d_st;
+        unsigned long long n_next = 0;
+        if (wc.n_low > 0) {
+            long long hc = 1;
+            while (hc < 2 * static_cast<long long>(wc.n_low)) hc <<= 1;
+            if (hc > g->hcap) return fail(DARTRAY_E_QUEUE, "merge table too small");
+            CK(cudaMemsetAsync(g->d_hkey, 0xff, hc * sizeof(unsigned long long), g->stream));
+            CK(cudaMemsetAsync(g->d_hcnt, 0, hc * sizeof(int), g->stream));
+            MergeArgs M{};
+            M.L = g->d_L;
+            M.L_I = g->d_LI;
+            M.n_low = static_cast<long long>(wc.n_low);
+            M.cap = g->cap;
+            M.hkey = g->d_hkey;
+            M.hcnt = g->d_hcnt;
+            M.hmem = g->d_hmem;
+            M.hcap = hc;
+            M.M_out = g->d_M[1 - par];
+            M.M_out_I = g->d_MI[1 - par];
+            M.wc = g->d_wc;
+            M.st = st;
+            M.nl = g->nl;
+            merge_insert_kernel<<<static_cast<unsigned>((M.n_low + kBlock - 1) / kBlock), kBlock, 0, g->stream>>>(M);
+            merge_emit_kernel<<<static_cast<unsigned>((hc + kBlock - 1) / kBlock), kBlock, 0, g->stream>>>(M);
+            g->launches += 2;
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(&wc, g->d_wc, sizeof(WaveCounters), cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            if (wc.status & ST_QUEUE) { *status = ST_QUEUE; return DARTRAY_OK; }
+            if (wc.status & ST_MERGE) return fail(DARTRAY_E_QUEUE, "merge table overflow");
+            n_next = wc.n_next;
+        }
+        *status = 0;
+        ++*waves;
+        nA = 4 * static_cast<long long>(wc.n_high);
+        nB = static_cast<long long>(n_next);
+        wave_kind = 1;
+        par = 1 - par;
+    }
+    return DARTRAY_OK;
+}
+
+struct PhaseResult {
+    double ledger[LG_N][kMaxLambda];
+    unsigned long long cnt[CT_N];
+    double f_u;
+    double pend_sum;
+};
+
+// One phase (mode: step 1, step 2, one scattering iteration).
+int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
+    cudaStream_t s = g->stream;
+    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
+    if (mode == MODE_SCATTER) g->cur = 1 - g->cur;
+    float *pend_src = g->d_pend[g->cur];
+    float *pend_dst = g->d_pend[1 - g->cur];
+    int n_src = 0;
+    int rc = build_sources(g, mode, pend_src, &n_src);
+    if (rc) return rc;
+    const double f_u = n_src > 0 ? 4.0 * g->P.a_rt / n_src : 0.0;  // Eq. 10
+    int kstart = g->P.k0;
+    if (mode == MODE_SCATTER)
+        for (int l = 0; l < g->nl; ++l) kstart = std::max(kstart, g->k_lam[l]);
+
+    MarchArgs base{};
+    base.src_leaf = g->d_src_leaf;
+    base.src_hint = g->d_src_hint;
+    base.src_pos = g->d_src_pos;
+    base.src_S = g->d_src_S;
+    base.cap = g->cap;
+    base.target = mode == MODE_LL ? g->d_ULL : g->d_U;
+    base.U_LL = g->d_ULL;
+    base.pend_src = pend_src;
+    base.pend_dst = pend_dst;
+    base.f_u = static_cast<float>(f_u);
+    base.r_pre = static_cast<float>(g->P.r_pre);
+    base.c_light = static_cast<float>(g->P.c_light);
+    base.split_c = 4.0 * kPi * static_cast<double>(g->P.n_rays_min);
+    base.merge_c = 4.0 * kPi * static_cast<double>(g->P.n_rays_max);
+    base.k_ray_max = g->P.k_ray_max;
+    base.merge = g->P.merge;
+    base.max_cross = g->P.max_cross;
+    base.wc = g->d_wc;
+    base.st = g->d_st;
+
+    long long batch = g->P.src_batch > 0 ? g->P.src_batch : n_src;
+    DevStats snap{};
+    CK(cudaMemcpyAsync(&snap, g->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (;;) {
+        // (re)start the phase: zero what it writes
+        if (mode == MODE_LL) {
+            CK(cudaMemsetAsync(g->d_ULL, 0, nU * sizeof(float), s));
+        } else {
+            if (mode == MODE_DIRECT) {
+                CK(cudaMemsetAsync(g->d_U, 0, nU * sizeof(float), s));
+            } else {
+                // U equals U_LL at the start of an iteration (U_LL <- U after each phase)
+                CK(cudaMemcpyAsync(g->d_U, g->d_ULL, nU * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            }
+            CK(cudaMemsetAsync(pend_dst, 0, g->sca_len * sizeof(float), s));
+        }
+        DevStats fresh = snap;
+        std::memset(fresh.ledger, 0, sizeof fresh.ledger);
+        CK(cudaMemcpyAsync(g->d_st, &fresh, sizeof(DevStats), cudaMemcpyHostToDevice, s));
+        long long waves = 0;
+        bool overflow = false;
+        for (long long lo = 0; lo < n_src; lo += batch) {
+            const int nb = static_cast<int>(std::min<long long>(batch, n_src - lo));
+            int status = 0;
+            rc = run_batch(g, mode, base, static_cast<int>(lo), nb, kstart, &status, &waves);
+            if (rc) return rc;
+            if (status == ST_QUEUE) { overflow = true; break; }
+        }
+        if (!overflow) {
+            DevStats out{};
+            CK(cudaMemcpyAsync(&out, g->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            out.cnt[CT_WAVES] += static_cast<unsigned long long>(waves);
+            out.cnt[CT_SOURCES] += static_cast<unsigned long long>(n_src);
+            CK(cudaMemcpyAsync(g->d_st, &out, sizeof(DevStats), cudaMemcpyHostToDevice, s));
+            std::memcpy(res->ledger, out.ledger, sizeof res->ledger);
+            std::memcpy(res->cnt, out.cnt, sizeof res->cnt);
+            break;
+        }
+        if (batch <= 1) return fail(DARTRAY_E_QUEUE, "ray queues overflow with a single source");
+        batch = std::max<long long>(1, batch / 4);
+    }
+    res->f_u = f_u;
+    res->pend_sum = 0.0;
+    if (mode != MODE_LL) {
+        CK(cudaMemsetAsync(g->d_sum, 0, sizeof(double), s));
+        accumulate_pending_kernel<<<4 * g->num_sms, kBlock, 0, s>>>(pend_dst, g->d_jtot, g->sca_len, g->d_sum);
+        ++g->launches;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(g->d_ULL, g->d_U, nU * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(&res->pend_sum, g->d_sum, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return DARTRAY_OK;
+}
+
+void fill_stats(const dartray_grid *g, const PhaseResult &r, dartray_stats *st) {
+    if (!st) return;
+    std::memset(st, 0, sizeof *st);
+    st->rays = r.cnt[CT_RAYS];
+    st->crossings = r.cnt[CT_CROSS];
+    st->splits = r.cnt[CT_SPLIT];
+    st->merges = r.cnt[CT_MERGE];
+    st->blocks = r.cnt[CT_BLOCK];
+    st->escapes = r.cnt[CT_ESCAPE];
+    st->cuts = r.cnt[CT_CUT];
+    st->lows = r.cnt[CT_LOW];
+    st->resumes = r.cnt[CT_RESUME];
+    st->waves = r.cnt[CT_WAVES];
+    st->sources = r.cnt[CT_SOURCES];
+    st->jsca_pixels = r.cnt[CT_JPIX];
+    for (int l = 0; l < g->nl; ++l) {
+        const double w = g->G.albedo[l];
+        st->emitted[l] = r.ledger[LG_EMITTED][l];
+        st->absorbed[l] = (1.0 - w) * r.ledger[LG_DEPOSITED][l];
+        st->scattered[l] = w * r.ledger[LG_DEPOSITED][l];
+        st->escaped[l] = r.ledger[LG_ESCAPED][l];
+        st->blocked[l] = r.ledger[LG_BLOCKED][l];
+        st->cut[l] = r.ledger[LG_CUT][l];
+        st->skipped[l] = r.ledger[LG_SKIPPED][l];
+    }
+    st->f_u = r.f_u;
+    st->l_sca2 = g->l_sca2;
+    st->kernel_launches = g->launches;
+}
+
+int set_device(dartray_grid *g) {
+    CK(cudaSetDevice(g->device));
+    return DARTRAY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dartray_params_default(dartray_params *p) {
+    if (!p) return fail(DARTRAY_E_INVAL, "null params");
+    std::memset(p, 0, sizeof *p);
+    p->a_rt = 0.05;
+    p->r_pre = -1.0;
+    p->f_l = 0.01;
+    p->c_light = 1.0;
+    p->n_rays_min = 5;
+    p->n_rays_max = 40;
+    p->k0 = 2;
+    p->k_ray_max = 13;
+    p->k_sca_cap = 3;
+    p->n_fwhm = 5;
+    p->merge = 1;
+    p->max_cross = 1 << 22;
+    p->max_waves = 200;
+    p->src_stride = 1;
+    p->src_offset = 0;
+    p->queue_rays = 1ll << 24;
+    p->src_batch = 0;
+    p->profile = 0;
+    return DARTRAY_OK;
+}
+
+int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *params, void *cuda_stream,
+                        dartray_grid **out) {
+    g_last_error.clear();
+    if (!desc || !out) return fail(DARTRAY_E_INVAL, "null argument");
+    *out = nullptr;
+    dartray_params P;
+    if (params) P = *params;
+    else dartray_params_default(&P);
+    const int nl = desc->n_lambda;
+    if (nl != 1 && nl != 2 && nl != 4 && nl != 8 && nl != 16)
+        return fail(DARTRAY_E_INVAL, "n_lambda must be 1, 2, 4, 8 or 16");
+    if (desc->n_leaf < 1 || desc->n_nodes < 1 || desc->n_point < 0) return fail(DARTRAY_E_INVAL, "bad sizes");
+    if (P.k0 < 0 || P.k0 > 13 || P.k_ray_max < P.k0 || P.k_ray_max > 13 || P.k_sca_cap < 0 || P.k_sca_cap > 3 ||
+        P.n_fwhm < 1 || P.n_rays_min < 0 || P.n_rays_max < 0 || P.src_stride < 1 || P.src_offset < 0 ||
+        P.src_offset >= P.src_stride || P.max_cross < 1 || P.max_waves < 1 || P.queue_rays < 1024 ||
+        !(P.c_light > 0) || P.a_rt < 0)
+        return fail(DARTRAY_E_INVAL, "invalid parameters");
+    const bool on_dev = desc->inputs_on_device != 0;
+    // host copies of the topology for validation and face links
+    std::vector<int32_t> fc, lon;
+    int rc = fetch_host(fc, desc->first_child, desc->n_nodes, on_dev);
+    if (rc) return rc;
+    rc = fetch_host(lon, desc->leaf_of_node, desc->n_nodes, on_dev);
+    if (rc) return rc;
+    std::vector<float> alb, gg;
+    rc = fetch_host(alb, desc->albedo, nl, on_dev);
+    if (rc) return rc;
+    rc = fetch_host(gg, desc->g, nl, on_dev);
+    if (rc) return rc;
+    for (int l = 0; l < nl; ++l)
+        if (!(alb[l] >= 0.f && alb[l] <= 1.f) || !(gg[l] > -1.f && gg[l] < 1.f))
+            return fail(DARTRAY_E_INVAL, "albedo must be in [0,1] and g in (-1,1)");
+
+    dartray_grid *g = new dartray_grid();
+    g->P = P;
+    g->stream = static_cast<cudaStream_t>(cuda_stream);
+    g->nl = nl;
+    g->n_leaf = desc->n_leaf;
+    g->n_nodes = desc->n_nodes;
+    g->n_point = desc->n_point;
+    auto bail = [&](int code) {
+        free_all(g);
+        delete g;
+        return code;
+    };
+    std::string err = build_topology(desc->nroot, desc->root_lo, desc->root_size, desc->n_nodes, desc->n_leaf,
+                                     fc.data(), lon.data(), &g->topo);
+    if (!err.empty()) return bail(fail(DARTRAY_E_INVAL, err));
+    if (cudaGetDevice(&g->device) != cudaSuccess) return bail(fail(DARTRAY_E_CUDA, "no CUDA device"));
+    cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (g->P.r_pre < 0) g->P.r_pre = 0.15 * desc->root_size * std::max({desc->nroot[0], desc->nroot[1], desc->nroot[2]});
+
+    // j_sca layout (Eq. 5)
+    long long off = 0;
+    for (int l = 0; l < nl; ++l) {
+        g->k_lam[l] = k_hp_host(gg[l], P.n_fwhm, P.k_sca_cap);
+        g->off_lam[l] = off;
+        off += static_cast<long long>(desc->n_leaf) * (12ll << (2 * g->k_lam[l]));
+    }
+    g->sca_len = off;
+
+    const size_t nU = static_cast<size_t>(desc->n_leaf) * nl;
+    const long long ndir = dir_tab_offset(kDirTabLevels + 1);
+    g->cap = P.queue_rays;
+    g->hcap = 1;
+    while (g->hcap < 2 * g->cap) g->hcap <<= 1;
+    const int n_all = desc->n_leaf + desc->n_point;
+    const int nblk = (n_all + kBlock - 1) / kBlock;
+#define AL(ptr, cnt)                                                                              \
+    do {                                                                                          \
+        cudaError_t e_ = dalloc(&(ptr), (cnt));                                                   \
+        if (e_ != cudaSuccess)                                                                    \
+            return bail(fail(DARTRAY_E_NOMEM, std::string("cudaMalloc ") + #ptr + ": " + cudaGetErrorString(e_))); \
+    } while (0)
+    AL(g->d_node_child, desc->n_nodes);
+    AL(g->d_node_box, desc->n_nodes);
+    AL(g->d_leaf_box, desc->n_leaf);
+    AL(g->d_rope, static_cast<size_t>(desc->n_leaf) * 6);
+    AL(g->d_dirtab, ndir);
+    AL(g->d_kr, nU);
+    AL(g->d_emis, nU);
+    AL(g->d_pxyz, static_cast<size_t>(desc->n_point) * 3);
+    AL(g->d_plum, static_cast<size_t>(desc->n_point) * nl);
+    AL(g->d_U, nU);
+    AL(g->d_ULL, nU);
+    AL(g->d_pend[0], g->sca_len);
+    AL(g->d_pend[1], g->sca_len);
+    AL(g->d_jtot, g->sca_len);
+    AL(g->d_flags, n_all);
+    AL(g->d_blocksum, nblk + 1);
+    AL(g->d_total, 1);
+    AL(g->d_src_idx, n_all);
+    AL(g->d_src_leaf, n_all);
+    AL(g->d_src_hint, n_all);
+    AL(g->d_src_pos, n_all);
+    AL(g->d_src_S, static_cast<size_t>(n_all) * nl);
+    for (int i = 0; i < 2; ++i) {
+        AL(g->d_H[i], g->cap);
+        AL(g->d_M[i], g->cap);
+        AL(g->d_HI[i], static_cast<size_t>(g->cap) * nl);
+        AL(g->d_MI[i], static_cast<size_t>(g->cap) * nl);
+    }
+    AL(g->d_L, g->cap);
+    AL(g->d_LI, static_cast<size_t>(g->cap) * nl);
+    AL(g->d_hkey, g->hcap);
+    AL(g->d_hcnt, g->hcap);
+    AL(g->d_hmem, g->hcap);
+    AL(g->d_wc, 1);
+    AL(g->d_st, 1);
+    AL(g->d_sum, 1);
+#undef AL
+    cudaStream_t s = g->stream;
+    auto up = [&](auto *dst, const auto *src, size_t cnt) { return copy_in(dst, src, cnt, false, s); };
+    if ((rc = up(g->d_node_child, g->topo.node_child.data(), desc->n_nodes))) return bail(rc);
+    if ((rc = up(reinterpret_cast<float *>(g->d_node_box), g->topo.node_box.data(), 4ull * desc->n_nodes))) return bail(rc);
+    if ((rc = up(reinterpret_cast<float *>(g->d_leaf_box), g->topo.leaf_box.data(), 4ull * desc->n_leaf))) return bail(rc);
+    if ((rc = up(g->d_rope, g->topo.leaf_rope.data(), 6ull * desc->n_leaf))) return bail(rc);
+    if ((rc = copy_in(g->d_kr, desc->kappa_rho, nU, on_dev, s))) return bail(rc);
+    if ((rc = copy_in(g->d_emis, desc->emissivity, nU, on_dev, s))) return bail(rc);
+    if ((rc = copy_in(g->d_pxyz, desc->point_xyz, 3ull * desc->n_point, on_dev, s))) return bail(rc);
+    if ((rc = copy_in(g->d_plum, desc->point_lum, static_cast<size_t>(desc->n_point) * nl, on_dev, s))) return bail(rc);
+    if (cudaMemsetAsync(g->d_U, 0, nU * sizeof(float), s) != cudaSuccess ||
+        cudaMemsetAsync(g->d_ULL, 0, nU * sizeof(float), s) != cudaSuccess ||
+        cudaMemsetAsync(g->d_pend[0], 0, g->sca_len * sizeof(float), s) != cudaSuccess ||
+        cudaMemsetAsync(g->d_pend[1], 0, g->sca_len * sizeof(float), s) != cudaSuccess ||
+        cudaMemsetAsync(g->d_jtot, 0, g->sca_len * sizeof(float), s) != cudaSuccess ||
+        cudaMemsetAsync(g->d_st, 0, sizeof(DevStats), s) != cudaSuccess)
+        return bail(fail(DARTRAY_E_CUDA, "memset failed"));
+    dirtab_kernel<<<static_cast<unsigned>((ndir + kBlock - 1) / kBlock), kBlock, 0, s>>>(g->d_dirtab, ndir);
+    ++g->launches;
+
+    DevGrid &G = g->G;
+    for (int a = 0; a < 3; ++a) {
+        G.nroot[a] = desc->nroot[a];
+        G.root_lo[a] = static_cast<float>(desc->root_lo[a]);
+    }
+    G.root_size = static_cast<float>(desc->root_size);
+    G.n_nodes = desc->n_nodes;
+    G.n_leaf = desc->n_leaf;
+    G.nl = nl;
+    G.n_point = desc->n_point;
+    G.node_child = g->d_node_child;
+    G.node_box = g->d_node_box;
+    G.leaf_box = g->d_leaf_box;
+    G.leaf_rope = g->d_rope;
+    G.kappa_rho = g->d_kr;
+    G.emis = g->d_emis;
+    G.point_xyz = g->d_pxyz;
+    G.point_lum = g->d_plum;
+    G.dirtab = g->d_dirtab;
+    for (int l = 0; l < nl; ++l) {
+        G.albedo[l] = alb[l];
+        G.g[l] = gg[l];
+        G.k_lam[l] = g->k_lam[l];
+        G.off_lam[l] = g->off_lam[l];
+    }
+    switch (nl) {
+    case 1: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<1, MODE_SCATTER>), g->num_sms); break;
+    case 2: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<2, MODE_SCATTER>), g->num_sms); break;
+    case 4: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<4, MODE_SCATTER>), g->num_sms); break;
+    case 8: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<8, MODE_SCATTER>), g->num_sms); break;
+    default: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<16, MODE_SCATTER>), g->num_sms); break;
+    }
+    if (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess ||
+        cudaEventCreate(&g->mev0) != cudaSuccess || cudaEventCreate(&g->mev1) != cudaSuccess)
+        return bail(fail(DARTRAY_E_CUDA, "event create failed"));
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bail(fail(DARTRAY_E_CUDA, cudaGetErrorString(e)));
+    const cudaError_t e2 = cudaGetLastError();
+    if (e2 != cudaSuccess) return bail(fail(DARTRAY_E_CUDA, cudaGetErrorString(e2)));
+    *out = g;
+    return DARTRAY_OK;
+}
+
+int dartray_direct(dartray_grid *g, dartray_stats *stats) {
+    g_last_error.clear();
+    if (!g) return fail(DARTRAY_E_INVAL, "null grid");
+    int rc = set_device(g);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(g->d_st, 0, sizeof(DevStats), g->stream));
+    CK(cudaMemsetAsync(g->d_jtot, 0, g->sca_len * sizeof(float), g->stream));
+    g->cur = 0;  // step 2 deposits into d_pend[1]
+    const long long l0 = g->launches;
+    g->march_ms = 0.0;
+    g->march_launches = 0;
+    CK(cudaEventRecord(g->ev0, g->stream));
+    PhaseResult r1{}, r2{};
+    if ((rc = run_phase(g, MODE_LL, &r1))) return rc;
+    if ((rc = run_phase(g, MODE_DIRECT, &r2))) return rc;
+    CK(cudaEventRecord(g->ev1, g->stream));
+    CK(cudaEventSynchronize(g->ev1));
+    g->l_sca2 = r2.pend_sum;
+    g->have_direct = true;
+    if (stats) {
+        fill_stats(g, r2, stats);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+        stats->gpu_ms = ms;
+        stats->kernel_launches = g->launches - l0;
+        stats->march_ms = g->march_ms;
+        stats->march_launches = g->march_launches;
+    }
+    return DARTRAY_OK;
+}
+
+int dartray_scatter_iter(dartray_grid *g, double *remaining_frac, dartray_stats *stats) {
+    g_last_error.clear();
+    if (!g) return fail(DARTRAY_E_INVAL, "null grid");
+    if (!g->have_direct) return fail(DARTRAY_E_STATE, "dartray_direct must run first");
+    int rc = set_device(g);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(g->d_st, 0, sizeof(DevStats), g->stream));
+    const long long l0 = g->launches;
+    g->march_ms = 0.0;
+    g->march_launches = 0;
+    CK(cudaEventRecord(g->ev0, g->stream));
+    PhaseResult r{};
+    if ((rc = run_phase(g, MODE_SCATTER, &r))) return rc;
+    CK(cudaEventRecord(g->ev1, g->stream));
+    CK(cudaEventSynchronize(g->ev1));
+    if (remaining_frac) *remaining_frac = g->l_sca2 > 0 ? r.pend_sum / g->l_sca2 : 0.0;
+    if (stats) {
+        fill_stats(g, r, stats);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+        stats->gpu_ms = ms;
+        stats->kernel_launches = g->launches - l0;
+        stats->march_ms = g->march_ms;
+        stats->march_launches = g->march_launches;
+    }
+    return DARTRAY_OK;
+}
+
+int dartray_rfed(dartray_grid *g, float *U, float *L_abs, int dst_is_device) {
+    g_last_error.clear();
+    if (!g) return fail(DARTRAY_E_INVAL, "null grid");
+    int rc = set_device(g);
+    if (rc) return rc;
+    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
+    const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (U) CK(cudaMemcpyAsync(U, g->d_U, nU * sizeof(float), k, g->stream));
+    if (L_abs) {
+        float *dst = L_abs;
+        if (!dst_is_device) CK(cudaMalloc(reinterpret_cast<void **>(&dst), nU * sizeof(float)));
+        labs_kernel<<<static_cast<unsigned>((nU + kBlock - 1) / kBlock), kBlock, 0, g->stream>>>(
+            g->G, g->d_U, static_cast<float>(g->P.c_light), dst);
+        ++g->launches;
+        CK(cudaGetLastError());
+        if (!dst_is_device) {
+            CK(cudaMemcpyAsync(L_abs, dst, nU * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            cudaFree(dst);
+        }
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    return DARTRAY_OK;
+}
+
+int dartray_jsca_layout(const dartray_grid *g, int32_t *k_lambda, int64_t *offsets, int64_t *total_len) {
+    if (!g) return fail(DARTRAY_E_INVAL, "null grid");
+    for (int l = 0; l < g->nl; ++l) {
+        if (k_lambda) k_lambda[l] = g->k_lam[l];
+        if (offsets) offsets[l] = g->off_lam[l];
+    }
+    if (total_len) *total_len = g->sca_len;
+    return DARTRAY_OK;
+}
+
+int dartray_jsca(dartray_grid *g, int which, float *out, int dst_is_device) {
+    g_last_error.clear();
+    if (!g || !out || which < 0 || which > 1) return fail(DARTRAY_E_INVAL, "bad argument");
+    int rc = set_device(g);
+    if (rc) return rc;
+    const float *src = which == 0 ? g->d_jtot : g->d_pend[1 - g->cur];
+    CK(cudaMemcpyAsync(out, src, g->sca_len * sizeof(float),
+                       dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return DARTRAY_OK;
+}
+
+int dartray_map(dartray_grid *g, const double observer[3], int32_t nside_k, int32_t max_sub, int32_t use_jsca,
+                float *map, int dst_is_device) {
+    g_last_error.clear();
+    if (!g || !observer || !map) return fail(DARTRAY_E_INVAL, "null argument");
+    if (nside_k < 0 || nside_k > 10 || max_sub < 0 || max_sub > 6) return fail(DARTRAY_E_INVAL, "bad map size");
+    int rc = set_device(g);
+    if (rc) return rc;
+    const long long npix = 12ll << (2 * nside_k);
+    const size_t nmap = static_cast<size_t>(npix) * g->nl;
+    float *dst = map;
+    if (!dst_is_device) CK(cudaMalloc(reinterpret_cast<void **>(&dst), nmap * sizeof(float)));
+    CK(cudaMemsetAsync(dst, 0, nmap * sizeof(float), g->stream));
+    MapArgs M{};
+    for (int a = 0; a < 3; ++a) M.obs[a] = static_cast<float>(observer[a]);
+    M.nside_k = nside_k;
+    M.max_sub = max_sub;
+    M.jsca = use_jsca ? g->d_jtot : nullptr;
+    M.map = dst;
+    const int blocks = (g->n_leaf + kBlock - 1) / kBlock;
+    rc = launch_map(g->G, M, blocks, g->stream);
+    if (rc) return fail(DARTRAY_E_INVAL, "unsupported n_lambda for maps");
+    ++g->launches;
+    CK(cudaGetLastError());
+    if (!dst_is_device) {
+        CK(cudaMemcpyAsync(map, dst, nmap * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        cudaFree(dst);
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    return DARTRAY_OK;
+}
+
+int dartray_state_save(dartray_grid *g, const char *path) {
+    g_last_error.clear();
+    if (!g || !path) return fail(DARTRAY_E_INVAL, "null argument");
+    int rc = set_device(g);
+    if (rc) return rc;
+    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
+    std::vector<float> buf(std::max<size_t>(nU, g->sca_len));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(DARTRAY_E_INVAL, std::string("cannot open ") + path);
+    const char magic[8] = {'D', 'R', 'T', 'S', 'T', 'A', 'T', '1'};
+    long long hdr[4] = {g->n_leaf, g->nl, g->sca_len, g->have_direct ? 1 : 0};
+    bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof hdr, 1, f) == 1 &&
+              std::fwrite(&g->l_sca2, sizeof(double), 1, f) == 1;
+    const float *arrs[5] = {g->d_U, g->d_ULL, g->d_pend[g->cur], g->d_pend[1 - g->cur], g->d_jtot};
+    const size_t lens[5] = {nU, nU, static_cast<size_t>(g->sca_len), static_cast<size_t>(g->sca_len),
+                            static_cast<size_t>(g->sca_len)};
+    for (int i = 0; i < 5 && ok; ++i) {
+        if (cudaMemcpy(buf.data(), arrs[i], lens[i] * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(f);
+            return fail(DARTRAY_E_CUDA, "copy failed");
+        }
+        ok = std::fwrite(buf.data(), sizeof(float), lens[i], f) == lens[i];
+    }
+    std::fclose(f);
+    return ok ? DARTRAY_OK : fail(DARTRAY_E_INVAL, "write failed");
+}
+
+int dartray_state_load(dartray_grid *g, const char *path) {
+    g_last_error.clear();
+    if (!g || !path) return fail(DARTRAY_E_INVAL, "null argument");
+    int rc = set_device(g);
+    if (rc) return rc;
+    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(DARTRAY_E_INVAL, std::string("cannot open ") + path);
+    char magic[8];
+    long long hdr[4];
+    double l2 = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "DRTSTAT1", 8) == 0 &&
+              std::fread(hdr, sizeof hdr, 1, f) == 1 && std::fread(&l2, sizeof(double), 1, f) == 1 &&
+              hdr[0] == g->n_leaf && hdr[1] == g->nl && hdr[2] == g->sca_len;
+    if (!ok) {
+        std::fclose(f);
+        return fail(DARTRAY_E_INVAL, "state file does not match this grid");
+    }
+    std::vector<float> buf(std::max<size_t>(nU, g->sca_len));
+    g->cur = 0;
+    float *arrs[5] = {g->d_U, g->d_ULL, g->d_pend[0], g->d_pend[1], g->d_jtot};
+    const size_t lens[5] = {nU, nU, static_cast<size_t>(g->sca_len), static_cast<size_t>(g->sca_len),
+                            static_cast<size_t>(g->sca_len)};
+    for (int i = 0; i < 5 && ok; ++i) {
+        ok = std::fread(buf.data(), sizeof(float), lens[i], f) == lens[i];
+        if (ok && cudaMemcpy(arrs[i], buf.data(), lens[i] * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+            std::fclose(f);
+            return fail(DARTRAY_E_CUDA, "copy failed");
+        }
+    }
+    std::fclose(f);
+    if (!ok) return fail(DARTRAY_E_INVAL, "truncated state file");
+    g->l_sca2 = l2;
+    g->have_direct = hdr[3] != 0;
+    return DARTRAY_OK;
+}
+
+void dartray_grid_destroy(dartray_grid *g) {
+    if (!g) return;
+    cudaSetDevice(g->device);
+    cudaStreamSynchronize(g->stream);
+    free_all(g);
+    delete g;
+}
+
+const char *dartray_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,30 @@
+// Host-side grid preparation shared by the CUDA translation unit: validation
+// of the flattened forest, node boxes, and leaf face links ("ropes").
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace dartray {
+
+struct HostTopo {
+    // node_child[node] = first child (>= 0) or -(leaf + 1) for a leaf
+    std::vector<int32_t> node_child;
+    // node boxes: lo x, lo y, lo z, side (exact in float32, validated)
+    std::vector<float> node_box;   // [n_nodes * 4]
+    std::vector<float> leaf_box;   // [n_leaf * 4]
+    std::vector<int32_t> leaf_node;
+    // leaf_rope[leaf * 6 + 2 * axis + (side > 0)]: the node on the other side
+    // of that face, of the same or larger size, or -1 on the model boundary
+    std::vector<int32_t> leaf_rope;
+    int max_depth = 0;
+};
+
+// Validates the description (tree structure, exact float32 face coordinates)
+// and fills *t.  Returns "" on success, else an error message.
+std::string build_topology(const int32_t nroot[3], const double root_lo[3], double root_size,
+                           int32_t n_nodes, int32_t n_leaf, const int32_t *first_child,
+                           const int32_t *leaf_of_node, HostTopo *t);
+
+}  // namespace dartray

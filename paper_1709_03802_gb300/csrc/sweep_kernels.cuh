@@ -1,0 +1,727 @@
+// Kernels of the ray-propagation sweep (Sect. 2, Sect. 3.1-3.5 of the paper):
+// the ray marcher with split/merge/blocking tests and warp-cooperative
+// deposit of the Henyey-Greenstein scattering source function, the low-list
+// merge, source-table construction and the end-of-phase updates.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace dartray {
+
+enum { MODE_LL = 0, MODE_DIRECT = 1, MODE_SCATTER = 2 };
+constexpr int kBlock = 256;
+constexpr int kPixTab = 1020;  // pixel centres of levels 0..3 (j_sca levels)
+
+struct MarchArgs {
+    // wave input: [0, nA) implicit (seeds of sources src_lo.., or the 4 children
+    // of each high-list parent), [nA, nA + nB) explicit records
+    int wave_kind;  // 0 seeds, 1 children + explicit
+    long long nA, nB;
+    const RayRec *H_in;
+    const float *H_in_I;
+    const RayRec *M_in;
+    const float *M_in_I;
+    int kstart;
+    int src_lo;
+    const int *src_leaf;     // source cell (or the leaf holding a point source)
+    const int *src_hint;     // start leaf of the seeds (-1: locate)
+    const float4 *src_pos;   // source position
+    const float *src_S;      // [n_src][nl] per-sr luminosity (direct light)
+    // outputs
+    RayRec *H_out;
+    float *H_out_I;
+    RayRec *L_out;
+    float *L_out_I;
+    long long cap;           // records per queue (I arrays are [nl][cap])
+    // fields
+    float *target;           // U_LL (step 1) or U
+    const float *U_LL;
+    const float *pend_src;
+    float *pend_dst;
+    float f_u, r_pre, c_light;
+    double split_c, merge_c; // 4 pi N_rays, 4 pi N_rays^max
+    int k_ray_max, merge, max_cross;
+    WaveCounters *wc;
+    DevStats *st;
+};
+
+__device__ inline float omega_of(int k) {
+    return static_cast<float>(4.0 * kPi / (12.0 * static_cast<double>(1ull << (2 * k))));
+}
+
+// Warp-aggregated append: returns this lane's slot (valid only where want).
+__device__ inline unsigned long long warp_append(bool want, unsigned long long *counter, int lane) {
+    const unsigned m = __ballot_sync(kFull, want);
+    if (!m) return 0;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, static_cast<unsigned long long>(__popc(m)));
+    base = __shfl_sync(kFull, base, leader);
+    return base + __popc(m & ((1u << lane) - 1u));
+}
+
+template <int NL>
+__device__ inline void flush_ledger(double (*sh_led)[kMaxLambda], int slot, const float *v, float scale) {
+#pragma unroll
+    for (int l = 0; l < NL; ++l)
+        if (v[l] != 0.f) atomicAdd(&sh_led[slot][l], static_cast<double>(v[l]) * scale);
+}
+
+/*
+ * One wave of rays.  Persistent warps: each lane owns one ray and marches it
+ * cell by cell; lanes that finish take the next ray of the wave.  Per
+ * crossing (Sect. 2, 3.1.1, 3.2, 3.5):
+ *   - segment [d, t_exit) of the current leaf, dtau = kappa*rho*ds;
+ *   - outside the source cell: step 1 stops rays at d >= R_pre; steps 2-3
+ *     mark wavelengths with dU = <I>/(r^2 c) < f_U U_LL negligible and block
+ *     the ray when all are (Eq. 1 with the Sect. 3.5 dU, Omega_INT = L^2/r^2);
+ *     Eq. 2 sends the ray to the high list, Eq. 3 to the low list (both
+ *     compared exactly in double);
+ *   - otherwise U += I Omega_k ds <I>/I / (V c) and the scattered luminosity
+ *     albedo I Omega_k (1 - e^-dtau) is spread over the cell's j_sca pixels
+ *     with normalised HG weights (Eq. 4) -- all 32 lanes of the warp share the
+ *     pixel loop of each depositing lane.
+ */
+template <int NL, int MODE>
+__global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const MarchArgs A) {
+    __shared__ float4 sh_pix[kPixTab];
+    __shared__ double sh_led[LG_N][kMaxLambda];
+    __shared__ unsigned long long sh_cnt[CT_N];
+    for (int i = threadIdx.x; i < kPixTab; i += blockDim.x) sh_pix[i] = G.dirtab[i];
+    for (int i = threadIdx.x; i < LG_N * kMaxLambda; i += blockDim.x) (&sh_led[0][0])[i] = 0.0;
+    if (threadIdx.x < CT_N) sh_cnt[threadIdx.x] = 0;
+    __syncthreads();
+
+    const int lane = threadIdx.x & (kWarp - 1);
+    const long long n_total = A.nA + A.nB;
+    float hgB[NL], hgC[NL], alb[NL];
+    int npx[NL], pixbase[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        hgB[l] = 1.f + G.g[l] * G.g[l];
+        hgC[l] = 2.f * G.g[l];
+        alb[l] = G.albedo[l];
+        npx[l] = 12 << (2 * G.k_lam[l]);
+        pixbase[l] = static_cast<int>(dir_tab_offset(G.k_lam[l]));
+    }
+
+    bool active = false;
+    int src = 0, lev = 0, kind = 0, leaf = -1, srcleaf = -1, ncross = 0, entry_axis = -1;
+    unsigned long long pix = 0;
+    float3 xs = make_float3(0, 0, 0), n = make_float3(0, 0, 1);
+    float d = 0.f, supp = 0.f, omega_k = 0.f, entry_coord = 0.f;
+    float4 box = make_float4(0, 0, 0, 0);
+    bool first = true;
+    float I[NL], Z[NL], acc_dep[NL], acc_skip[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) { I[l] = 0.f; Z[l] = 1.f; acc_dep[l] = 0.f; acc_skip[l] = 0.f; }
+    unsigned c_rays = 0, c_cross = 0, c_split = 0, c_block = 0, c_escape = 0, c_cut = 0, c_low = 0;
+    unsigned long long c_jpix = 0;  // j_sca pixels updated (lane 0 of each warp counts)
+
+    for (;;) {
+        // ---------------------------------------------------------- fetch
+        const unsigned idle = __ballot_sync(kFull, !active);
+        bool started = false;
+        if (idle) {
+            const int leader = __ffs(idle) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&A.wc->fetch, static_cast<unsigned long long>(__popc(idle)));
+            base = __shfl_sync(kFull, base, leader);
+            if (!active) {
+                const long long idx = static_cast<long long>(base + __popc(idle & ((1u << lane) - 1u)));
+                if (idx < n_total) {
+                    started = true;
+                    active = true;
+                    int hint = -1;
+                    int par_axis = -1;
+                    float par_coord = 0.f;
+                    unsigned long long par_pix = 0;
+                    supp = 0.f;
+                    entry_axis = -1;
+                    entry_coord = 0.f;
+                    if (idx < A.nA) {
+                        if (A.wave_kind == 0) {
+                            const long long npix0 = 12ll << (2 * A.kstart);
+                            src = A.src_lo + static_cast<int>(idx / npix0);
+                            pix = static_cast<unsigned long long>(idx % npix0);
+                            lev = A.kstart;
+                            kind = kSeed;
+                            d = 0.f;
+                            hint = A.src_hint[src];
+                            const float om = omega_of(lev);
+#pragma unroll
+                            for (int l = 0; l < NL; ++l) {
+                                float s;
+                                if (MODE == MODE_SCATTER) {
+                                    const int kl = G.k_lam[l];
+                                    const unsigned long long q = pix >> (2 * (lev - kl));
+                                    s = A.pend_src[G.off_lam[l] + static_cast<long long>(A.src_leaf[src]) * npx[l] + q] /
+                                        omega_of(kl);
+                                } else {
+                                    s = A.src_S[static_cast<long long>(src) * NL + l];
+                                }
+                                I[l] = s;
+                                if (s != 0.f) atomicAdd(&sh_led[LG_EMITTED][l], static_cast<double>(s) * om);
+                            }
+                        } else {
+                            const long long pi_ = idx >> 2;
+                            const RayRec r = A.H_in[pi_];
+                            src = r.src;
+                            lev = rr_lev(r.meta) + 1;
+                            pix = r.pix * 4ull + static_cast<unsigned long long>(idx & 3);
+                            kind = kChild;
+                            d = r.d;
+                            par_axis = rr_axis(r.meta);
+                            par_coord = r.plane;
+                            par_pix = r.pix;
+#pragma unroll
+                            for (int l = 0; l < NL; ++l) I[l] = A.H_in_I[l * A.cap + pi_];
+                        }
+                    } else {
+                        const long long mi = idx - A.nA;
+                        const RayRec r = A.M_in[mi];
+                        src = r.src;
+                        lev = rr_lev(r.meta);
+                        kind = rr_kind(r.meta);
+                        pix = r.pix;
+                        d = r.d;
+                        hint = r.hint;
+                        supp = r.supp;
+                        if (kind == kResumed) {  // resumes on the face it stopped at
+                            entry_axis = rr_axis(r.meta);
+                            entry_coord = r.plane;
+                        }
+#pragma unroll
+                        for (int l = 0; l < NL; ++l) I[l] = A.M_in_I[l * A.cap + mi];
+                    }
+                    const float4 sp = A.src_pos[src];
+                    xs = make_float3(sp.x, sp.y, sp.z);
+                    srcleaf = A.src_leaf[src];
+                    n = ray_dir(G, lev, pix);
+                    omega_k = omega_of(lev);
+                    if (hint >= 0) {
+                        leaf = hint;
+                    } else {
+                        float3 p = make_float3(fmaf(d, n.x, xs.x), fmaf(d, n.y, xs.y), fmaf(d, n.z, xs.z));
+                        // a child sharing its parent's direction component along
+                        // the parent's entry-face axis starts exactly on that face
+                        if (par_axis >= 0) {
+                            const float3 np_ = ray_dir(G, lev - 1, par_pix);
+                            const float cn = par_axis == 0 ? n.x : (par_axis == 1 ? n.y : n.z);
+                            const float cp = par_axis == 0 ? np_.x : (par_axis == 1 ? np_.y : np_.z);
+                            if (cn == cp) {
+                                if (par_axis == 0) p.x = par_coord;
+                                else if (par_axis == 1) p.y = par_coord;
+                                else p.z = par_coord;
+                                entry_axis = par_axis;
+                                entry_coord = par_coord;
+                            }
+                        }
+                        leaf = locate_root(G, p, n);
+                    }
+                    if (leaf >= 0) box = __ldg(&G.leaf_box[leaf]);
+                    first = true;
+                    ncross = 0;
+                    ++c_rays;
+                }
+            }
+        }
+        if (!__any_sync(kFull, active)) break;
+
+        // ------------------------------- HG normalisation of new rays (shared)
+        if (MODE != MODE_LL) {
+            unsigned m = __ballot_sync(kFull, started);
+            while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                const float nx = __shfl_sync(kFull, n.x, j), ny = __shfl_sync(kFull, n.y, j),
+                            nz = __shfl_sync(kFull, n.z, j);
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    float part = 0.f;
+                    for (int q = lane; q < npx[l]; q += kWarp) {
+                        const float4 pd = sh_pix[pixbase[l] + q];
+                        const float r = rsqrtf(hgB[l] - hgC[l] * (pd.x * nx + pd.y * ny + pd.z * nz));
+                        part += r * r * r;
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+                    if (lane == j) Z[l] = part;
+                }
+            }
+        }
+
+        // ---------------------------------------------------------- crossing
+        // outcome: 0 continue, 1 finished, 2 high list, 3 low list
+        int outcome = 1;
+        float sca[NL];
+        float te = 0.f;
+        int tie = 0;
+        float bnd[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int l = 0; l < NL; ++l) sca[l] = 0.f;
+        if (active) {
+            if (leaf < 0) {
+                float tmp[NL];
+#pragma unroll
+                for (int l = 0; l < NL; ++l) tmp[l] = I[l];
+                flush_ledger<NL>(sh_led, LG_ESCAPED, tmp, omega_k);
+                ++c_escape;
+                outcome = 1;
+            } else if (++ncross > A.max_cross) {
+                atomicOr(&A.wc->status, ST_CROSS_CAP);
+                if (atomicCAS(&A.wc->dbg_set, 0, 1) == 0) {
+                    A.wc->dbg_src = src; A.wc->dbg_lev = lev; A.wc->dbg_kind = kind; A.wc->dbg_leaf = leaf;
+                    A.wc->dbg_pix = pix; A.wc->dbg_d = d; A.wc->dbg_te = box.w; A.wc->dbg_prev = srcleaf;
+                }
+                outcome = 1;
+            } else {
+                ++c_cross;
+                const float inf = __int_as_float(0x7f800000);
+                bnd[0] = n.x > 0.f ? box.x + box.w : box.x;
+                bnd[1] = n.y > 0.f ? box.y + box.w : box.y;
+                bnd[2] = n.z > 0.f ? box.z + box.w : box.z;
+                const float tx = n.x != 0.f ? (bnd[0] - xs.x) / n.x : inf;
+                const float ty = n.y != 0.f ? (bnd[1] - xs.y) / n.y : inf;
+                const float tz = n.z != 0.f ? (bnd[2] - xs.z) / n.z : inf;
+                te = fminf(tx, fminf(ty, tz));
+                tie = (tx == te ? 1 : 0) | (ty == te ? 2 : 0) | (tz == te ? 4 : 0);
+                if (tie == 0) {  // non-finite direction: never expected, never indexed
+                    atomicOr(&A.wc->status, ST_NOPROGRESS);
+                    active = false;
+                }
+                const float ds = fmaxf(te - d, 0.f);
+                const float L = box.w, V = L * L * L;
+                float fac[NL], T[NL], kr[NL];
+                bool neg[NL];
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    kr[l] = __ldg(&G.kappa_rho[static_cast<long long>(leaf) * NL + l]);
+                    const float dtau = kr[l] * ds;
+                    fac[l] = dtau > 0.f ? -expm1f(-dtau) / dtau : 1.f;
+                    T[l] = expf(-dtau);
+                    neg[l] = false;
+                }
+                outcome = active ? 0 : 1;
+                if (outcome == 0 && leaf != srcleaf) {
+                    // exact (double, uncontracted) geometry of the beam tests
+                    const double Ld = static_cast<double>(L);
+                    const double hx = __dmul_rn(0.5, Ld);
+                    const double dx = __dsub_rn(__dadd_rn(static_cast<double>(box.x), hx), static_cast<double>(xs.x));
+                    const double dy = __dsub_rn(__dadd_rn(static_cast<double>(box.y), hx), static_cast<double>(xs.y));
+                    const double dz = __dsub_rn(__dadd_rn(static_cast<double>(box.z), hx), static_cast<double>(xs.z));
+                    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                    if (MODE == MODE_LL) {
+                        if (d >= A.r_pre) {
+                            float tmp[NL];
+#pragma unroll
+                            for (int l = 0; l < NL; ++l) tmp[l] = I[l];
+                            flush_ledger<NL>(sh_led, LG_CUT, tmp, omega_k);
+                            ++c_cut;
+                            outcome = 1;
+                        }
+                    } else {
+                        const float r2f = static_cast<float>(r2);
+                        bool all = true;
+#pragma unroll
+                        for (int l = 0; l < NL; ++l) {
+                            const float dU = (I[l] * fac[l]) / (r2f * A.c_light);
+                            neg[l] = dU < A.f_u * __ldg(&A.U_LL[static_cast<long long>(leaf) * NL + l]);
+                            all = all && neg[l];
+                        }
+                        if (all) {
+                            float tmp[NL];
+#pragma unroll
+                            for (int l = 0; l < NL; ++l) tmp[l] = I[l];
+                            flush_ledger<NL>(sh_led, LG_BLOCKED, tmp, omega_k);
+                            ++c_block;
+                            outcome = 1;
+                        }
+                    }
+                    if (outcome == 0) {
+                        const double beam = ldexp(12.0, 2 * lev);
+                        const double rhs = __dmul_rn(__dmul_rn(beam, Ld), Ld);
+                        if (!(first && kind == kMerged) && lev < A.k_ray_max && __dmul_rn(A.split_c, r2) > rhs) {
+                            outcome = 2;
+                            ++c_split;
+                        } else if (A.merge && lev > 0 && !first && L != supp && __dmul_rn(A.merge_c, r2) < rhs) {
+                            outcome = 3;
+                            ++c_low;
+                        }
+                    }
+                }
+                if (outcome == 0) {
+#pragma unroll
+                    for (int l = 0; l < NL; ++l) {
+                        const float P_in = I[l] * omega_k;
+                        const float lost = P_in * kr[l] * ds * fac[l];
+                        if (neg[l]) {
+                            acc_skip[l] += lost;
+                        } else {
+                            const float du = P_in * ds * fac[l] / (V * A.c_light);
+                            if (du != 0.f) atomicAdd(&A.target[static_cast<long long>(leaf) * NL + l], du);
+                            acc_dep[l] += lost;
+                            if (MODE != MODE_LL) sca[l] = alb[l] * lost / Z[l];
+                        }
+                        I[l] *= T[l];
+                    }
+                }
+            }
+        }
+
+        // ------------------------------------------ high / low list appends
+        {
+            const bool wh = active && outcome == 2;
+            const unsigned long long slot = warp_append(wh, &A.wc->n_high, lane);
+            if (wh) {
+                if (slot < static_cast<unsigned long long>(A.cap)) {
+                    RayRec r;
+                    r.pix = pix; r.src = src; r.d = d; r.hint = -1; r.supp = 0.f; r.plane = entry_coord;
+                    r.meta = rr_meta(lev, kind, entry_axis);
+                    A.H_out[slot] = r;
+#pragma unroll
+                    for (int l = 0; l < NL; ++l) A.H_out_I[l * A.cap + slot] = I[l];
+                } else {
+                    atomicOr(&A.wc->status, ST_QUEUE);
+                }
+            }
+            const bool wl = active && outcome == 3;
+            const unsigned long long slot2 = warp_append(wl, &A.wc->n_low, lane);
+            if (wl) {
+                if (slot2 < static_cast<unsigned long long>(A.cap)) {
+                    RayRec r;
+                    r.pix = pix; r.src = src; r.d = d; r.hint = leaf; r.supp = box.w; r.plane = entry_coord;
+                    r.meta = rr_meta(lev, kind, entry_axis);
+                    A.L_out[slot2] = r;
+#pragma unroll
+                    for (int l = 0; l < NL; ++l) A.L_out_I[l * A.cap + slot2] = I[l];
+                } else {
+                    atomicOr(&A.wc->status, ST_QUEUE);
+                }
+            }
+        }
+
+        // ------------------------------- warp-cooperative j_sca deposit (Eq. 4)
+        if (MODE != MODE_LL) {
+            bool has = false;
+#pragma unroll
+            for (int l = 0; l < NL; ++l) has = has || (sca[l] > 0.f);
+            unsigned m = __ballot_sync(kFull, active && outcome == 0 && has);
+            while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                const int lj = __shfl_sync(kFull, leaf, j);
+                const float nx = __shfl_sync(kFull, n.x, j), ny = __shfl_sync(kFull, n.y, j),
+                            nz = __shfl_sync(kFull, n.z, j);
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    const float coef = __shfl_sync(kFull, sca[l], j);
+                    if (coef == 0.f) continue;
+                    c_jpix += (lane == 0) ? static_cast<unsigned>(npx[l]) : 0u;
+                    float *row = A.pend_dst + G.off_lam[l] + static_cast<long long>(lj) * npx[l];
+                    for (int q = lane; q < npx[l]; q += kWarp) {
+                        const float4 pd = sh_pix[pixbase[l] + q];
+                        const float r = rsqrtf(hgB[l] - hgC[l] * (pd.x * nx + pd.y * ny + pd.z * nz));
+                        atomicAdd(row + q, coef * (r * r * r));
+                    }
+                }
+            }
+        }
+
+        // ---------------------------------------------------------- advance
+        if (active) {
+            if (outcome == 0) {
+                d = fmaxf(te, d);
+                entry_axis = __ffs(tie) - 1;
+                entry_coord = bnd[entry_axis];
+                // exit point on the closed box of the cell being left (clamped:
+                // rounding must not put it in a cell behind the ray)
+                const float3 pe = make_float3(
+                    (tie & 1) ? bnd[0] : fminf(fmaxf(fmaf(te, n.x, xs.x), box.x), box.x + box.w),
+                    (tie & 2) ? bnd[1] : fminf(fmaxf(fmaf(te, n.y, xs.y), box.y), box.y + box.w),
+                    (tie & 4) ? bnd[2] : fminf(fmaxf(fmaf(te, n.z, xs.z), box.z), box.z + box.w));
+                const int nxt = next_leaf(G, leaf, tie, pe, n);
+                if (nxt < 0) {
+                    float tmp[NL];
+#pragma unroll
+                    for (int l = 0; l < NL; ++l) tmp[l] = I[l];
+                    flush_ledger<NL>(sh_led, LG_ESCAPED, tmp, omega_k);
+                    ++c_escape;
+                    outcome = 1;
+                } else if (nxt == leaf) {
+                    atomicOr(&A.wc->status, ST_NOPROGRESS);
+                    outcome = 1;
+                } else {
+                    leaf = nxt;
+                    box = __ldg(&G.leaf_box[leaf]);
+                    if (supp != 0.f && box.w != supp) supp = 0.f;
+                    first = false;
+                }
+            }
+            if (outcome != 0) {
+                flush_ledger<NL>(sh_led, LG_DEPOSITED, acc_dep, 1.f);
+                flush_ledger<NL>(sh_led, LG_SKIPPED, acc_skip, 1.f);
+#pragma unroll
+                for (int l = 0; l < NL; ++l) { acc_dep[l] = 0.f; acc_skip[l] = 0.f; }
+                active = false;
+            }
+        }
+    }
+
+    // ---------------------------------------------------------- flush
+    atomicAdd(&sh_cnt[CT_RAYS], static_cast<unsigned long long>(c_rays));
+    atomicAdd(&sh_cnt[CT_CROSS], static_cast<unsigned long long>(c_cross));
+    atomicAdd(&sh_cnt[CT_SPLIT], static_cast<unsigned long long>(c_split));
+    atomicAdd(&sh_cnt[CT_BLOCK], static_cast<unsigned long long>(c_block));
+    atomicAdd(&sh_cnt[CT_ESCAPE], static_cast<unsigned long long>(c_escape));
+    atomicAdd(&sh_cnt[CT_CUT], static_cast<unsigned long long>(c_cut));
+    atomicAdd(&sh_cnt[CT_LOW], static_cast<unsigned long long>(c_low));
+    if (c_jpix) atomicAdd(&sh_cnt[CT_JPIX], c_jpix);
+    __syncthreads();
+    for (int i = threadIdx.x; i < LG_N * NL; i += blockDim.x) {
+        const int s = i / NL, l = i % NL;
+        if (sh_led[s][l] != 0.0) atomicAdd(&A.st->ledger[s][l], sh_led[s][l]);
+    }
+    if (threadIdx.x < CT_N && sh_cnt[threadIdx.x]) atomicAdd(&A.st->cnt[threadIdx.x], sh_cnt[threadIdx.x]);
+}
+
+// ------------------------------------------------------------------ merging
+struct MergeArgs {
+    const RayRec *L;
+    const float *L_I;
+    long long n_low;
+    long long cap;
+    unsigned long long *hkey;  // [hcap], ~0 = empty
+    int *hcnt;
+    int4 *hmem;
+    long long hcap;
+    RayRec *M_out;
+    float *M_out_I;
+    WaveCounters *wc;
+    DevStats *st;
+    int nl;
+};
+
+__device__ inline unsigned long long merge_key(const RayRec &r) {
+    return (static_cast<unsigned long long>(static_cast<unsigned>(r.src)) << 32) |
+           (static_cast<unsigned long long>(rr_lev(r.meta)) << 28) | (r.pix >> 2);  // pix>>2 < 2^28 for k <= 13
+}
+
+__device__ inline unsigned long long hash64(unsigned long long k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+// Group low-list rays by (source, level, parent pixel).
+__global__ void merge_insert_kernel(const MergeArgs A) {
+    const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i >= A.n_low) return;
+    const unsigned long long key = merge_key(A.L[i]);
+    unsigned long long h = hash64(key) & static_cast<unsigned long long>(A.hcap - 1);
+    for (long long probe = 0; probe < A.hcap; ++probe) {
+        const unsigned long long prev = atomicCAS(&A.hkey[h], ~0ull, key);
+        if (prev == ~0ull || prev == key) {
+            const int c = atomicAdd(&A.hcnt[h], 1);
+            if (c < 4) reinterpret_cast<int *>(&A.hmem[h])[c] = static_cast<int>(i);
+            else atomicOr(&A.wc->status, ST_MERGE);
+            return;
+        }
+        h = (h + 1) & static_cast<unsigned long long>(A.hcap - 1);
+    }
+    atomicOr(&A.wc->status, ST_MERGE);
+}
+
+// Eq. 3 / Fig. 1: four siblings that stopped on the same grid plane become
+// their parent ray with the mean intensity at the mean distance; the others
+// resume where they stopped with the merge test suppressed until the cell
+// size changes.
+__global__ void merge_emit_kernel(const MergeArgs A) {
+    const long long h = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (h >= A.hcap || A.hkey[h] == ~0ull) return;
+    const int c = min(A.hcnt[h], 4);
+    int mem[4];
+    const int4 hm = A.hmem[h];
+    mem[0] = hm.x; mem[1] = hm.y; mem[2] = hm.z; mem[3] = hm.w;
+    bool ok = (A.hcnt[h] == 4);
+    if (ok) {
+        // order the siblings by pixel (sums in a fixed order)
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                if (A.L[mem[b]].pix < A.L[mem[a]].pix) { const int t = mem[a]; mem[a] = mem[b]; mem[b] = t; }
+        const RayRec &r0 = A.L[mem[0]];
+        for (int a = 1; a < 4; ++a) {
+            const RayRec &ra = A.L[mem[a]];
+            ok = ok && rr_axis(ra.meta) == rr_axis(r0.meta) && ra.plane == r0.plane;
+        }
+    }
+    if (ok) {
+        const unsigned long long slot = atomicAdd(&A.wc->n_next, 1ull);
+        if (slot >= static_cast<unsigned long long>(A.cap)) { atomicOr(&A.wc->status, ST_QUEUE); return; }
+        const RayRec &r0 = A.L[mem[0]];
+        RayRec m;
+        m.pix = r0.pix >> 2;
+        m.src = r0.src;
+        float dsum = 0.f;
+        for (int a = 0; a < 4; ++a) dsum += A.L[mem[a]].d;
+        m.d = dsum * 0.25f;
+        m.hint = -1;
+        m.supp = 0.f;
+        m.plane = 0.f;
+        m.meta = rr_meta(rr_lev(r0.meta) - 1, kMerged, -1);
+        A.M_out[slot] = m;
+        for (int l = 0; l < A.nl; ++l) {
+            float s = 0.f;
+            for (int a = 0; a < 4; ++a) s += A.L_I[l * A.cap + mem[a]];
+            A.M_out_I[l * A.cap + slot] = s * 0.25f;
+        }
+        atomicAdd(&A.st->cnt[CT_MERGE], 1ull);
+    } else {
+        const unsigned long long slot = atomicAdd(&A.wc->n_next, static_cast<unsigned long long>(c));
+        if (slot + c > static_cast<unsigned long long>(A.cap)) { atomicOr(&A.wc->status, ST_QUEUE); return; }
+        for (int a = 0; a < c; ++a) {
+            RayRec r = A.L[mem[a]];
+            r.meta = rr_meta(rr_lev(r.meta), kResumed, rr_axis(r.meta));
+            // r.hint (stop leaf) and r.supp (its side) were set by the marcher
+            A.M_out[slot + a] = r;
+            for (int l = 0; l < A.nl; ++l) A.M_out_I[l * A.cap + slot + a] = A.L_I[l * A.cap + mem[a]];
+        }
+        atomicAdd(&A.st->cnt[CT_RESUME], static_cast<unsigned long long>(c));
+    }
+}
+
+// ------------------------------------------------------------------ sources
+// flag[s] = 1 for sources of the phase: steps 1-2 emitting leaves and point
+// sources; scattering iterations leaves whose pending row is non-zero at some
+// wavelength; restricted to s % stride == offset.
+__global__ void source_flags_kernel(const DevGrid G, int mode, const float *pend_src, int stride, int offset,
+                                    int *flags) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_all = mode == MODE_SCATTER ? G.n_leaf : G.n_leaf + G.n_point;
+    if (s >= n_all) return;
+    int on = 0;
+    if (s < G.n_leaf) {
+        for (int l = 0; l < G.nl && !on; ++l) {
+            if (mode == MODE_SCATTER) {
+                const int np = 12 << (2 * G.k_lam[l]);
+                const float *row = pend_src + G.off_lam[l] + static_cast<long long>(s) * np;
+                for (int q = 0; q < np; ++q)
+                    if (row[q] > 0.f) { on = 1; break; }
+            } else {
+                on = G.emis[static_cast<long long>(s) * G.nl + l] > 0.f;
+            }
+        }
+    } else {
+        for (int l = 0; l < G.nl; ++l) on |= G.point_lum[static_cast<long long>(s - G.n_leaf) * G.nl + l] > 0.f;
+    }
+    flags[s] = (on && (s % stride) == offset) ? 1 : 0;
+}
+
+// Block-level exclusive scan of flags -> per-block totals.
+__global__ void scan_blocks_kernel(const int *flags, int n, int *block_sum) {
+    __shared__ int sh[kBlock / kWarp];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = i < n ? flags[i] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < kBlock / kWarp; ++w) s += sh[w];
+        block_sum[blockIdx.x] = s;
+    }
+}
+
+__global__ void scan_offsets_kernel(int *block_sum, int nblocks, int *total) {
+    // single thread: fine for <= a few 10^4 blocks
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int s = 0;
+        for (int b = 0; b < nblocks; ++b) { const int v = block_sum[b]; block_sum[b] = s; s += v; }
+        *total = s;
+    }
+}
+
+__global__ void scatter_compact_kernel(const int *flags, int n, const int *block_off, int *out) {
+    __shared__ int sh[kBlock / kWarp];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int f = i < n ? flags[i] : 0;
+    const unsigned b = __ballot_sync(kFull, f);
+    if (lane == 0) sh[w] = __popc(b);
+    __syncthreads();
+    int base = block_off[blockIdx.x];
+    for (int k = 0; k < w; ++k) base += sh[k];
+    if (f) out[base + __popc(b & ((1u << lane) - 1u))] = i;
+}
+
+// Source table from the compacted indices.
+__global__ void source_table_kernel(const DevGrid G, int mode, const int *idx, int n_src, int *src_leaf,
+                                    int *src_hint, float4 *src_pos, float *src_S) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_src) return;
+    const int s = idx[i];
+    if (s < G.n_leaf) {
+        const float4 b = G.leaf_box[s];
+        src_pos[i] = make_float4(b.x + 0.5f * b.w, b.y + 0.5f * b.w, b.z + 0.5f * b.w, 0.f);
+        src_leaf[i] = s;
+        src_hint[i] = s;
+        if (mode != MODE_SCATTER)
+            for (int l = 0; l < G.nl; ++l)
+                src_S[static_cast<long long>(i) * G.nl + l] = G.emis[static_cast<long long>(s) * G.nl + l] * (b.w * b.w * b.w);
+    } else {
+        const int ip = s - G.n_leaf;
+        const float3 p = make_float3(G.point_xyz[3 * ip], G.point_xyz[3 * ip + 1], G.point_xyz[3 * ip + 2]);
+        src_pos[i] = make_float4(p.x, p.y, p.z, 0.f);
+        src_leaf[i] = locate_root(G, p, make_float3(1.f, 1.f, 1.f));
+        src_hint[i] = -1;
+        for (int l = 0; l < G.nl; ++l)
+            src_S[static_cast<long long>(i) * G.nl + l] =
+                static_cast<float>(static_cast<double>(G.point_lum[static_cast<long long>(ip) * G.nl + l]) / (4.0 * kPi));
+    }
+}
+
+// ------------------------------------------------------------------ phase end
+// j_sca_total += pending; partial double sums of pending per block.
+__global__ void accumulate_pending_kernel(const float *pend, float *total, long long n, double *sum) {
+    __shared__ double sh[kBlock / kWarp];
+    double s = 0.0;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float v = pend[i];
+        total[i] += v;
+        s += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kBlock / kWarp; ++w) t += sh[w];
+        atomicAdd(sum, t);
+    }
+}
+
+// HEALPix pixel-centre table (levels 0..kDirTabLevels), computed in double.
+__global__ void dirtab_kernel(float4 *tab, long long n) {
+    const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    int k = 0;
+    while (k < kDirTabLevels && i >= dir_tab_offset(k + 1)) ++k;
+    double v[3];
+    pix2vec_d(k, static_cast<uint64_t>(i - dir_tab_offset(k)), v);
+    tab[i] = make_float4(static_cast<float>(v[0]), static_cast<float>(v[1]), static_cast<float>(v[2]), 0.f);
+}
+
+// L_abs = (1 - albedo) kappa*rho c V U
+__global__ void labs_kernel(const DevGrid G, const float *U, float c_light, float *L_abs) {
+    const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i >= static_cast<long long>(G.n_leaf) * G.nl) return;
+    const int leaf = static_cast<int>(i / G.nl), l = static_cast<int>(i % G.nl);
+    const float L = G.leaf_box[leaf].w;
+    L_abs[i] = (1.f - G.albedo[l]) * G.kappa_rho[i] * c_light * (L * L * L) * U[i];
+}
+
+}  // namespace dartray

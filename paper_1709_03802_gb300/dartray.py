@@ -1,0 +1,302 @@
+"""Thin Python binding of libdartray.so (include/dartray.h).
+
+Argument marshalling only: every step of the sweep runs in the CUDA library.
+The functions ``dartray_*`` mirror the C calls one to one; ``DartRay`` wraps a
+grid handle for convenience.  Inputs may be numpy arrays (host) or CUDA
+torch tensors (device); outputs are numpy arrays unless ``out`` is a CUDA
+tensor.  If the library is not built, loading fails with an error -- there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_LAMBDA = 16
+ERRORS = {0: "OK", -1: "INVAL", -2: "NOMEM", -3: "CUDA", -4: "QUEUE", -5: "LIMIT", -6: "STATE"}
+
+
+class DartRayError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class dartray_grid_desc(C.Structure):
+    _fields_ = [("nroot", C.c_int32 * 3), ("root_lo", C.c_double * 3), ("root_size", C.c_double),
+                ("n_nodes", C.c_int32), ("n_leaf", C.c_int32), ("n_lambda", C.c_int32),
+                ("first_child", C.c_void_p), ("leaf_of_node", C.c_void_p), ("kappa_rho", C.c_void_p),
+                ("emissivity", C.c_void_p), ("albedo", C.c_void_p), ("g", C.c_void_p),
+                ("n_point", C.c_int32), ("point_xyz", C.c_void_p), ("point_lum", C.c_void_p),
+                ("inputs_on_device", C.c_int32)]
+
+
+class dartray_params(C.Structure):
+    _fields_ = [("a_rt", C.c_double), ("r_pre", C.c_double), ("f_l", C.c_double), ("c_light", C.c_double),
+                ("n_rays_min", C.c_int32), ("n_rays_max", C.c_int32), ("k0", C.c_int32),
+                ("k_ray_max", C.c_int32), ("k_sca_cap", C.c_int32), ("n_fwhm", C.c_int32),
+                ("merge", C.c_int32), ("max_cross", C.c_int32), ("max_waves", C.c_int32),
+                ("src_stride", C.c_int32), ("src_offset", C.c_int32), ("queue_rays", C.c_int64),
+                ("src_batch", C.c_int64), ("profile", C.c_int32), ("reserved", C.c_int32)]
+
+
+_L = MAX_LAMBDA
+
+
+class dartray_stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("rays", "crossings", "splits", "merges", "blocks", "escapes",
+                                          "cuts", "lows", "resumes", "waves", "sources")] + \
+               [(n, C.c_double * _L) for n in ("emitted", "absorbed", "scattered", "escaped", "blocked",
+                                                "cut", "skipped")] + \
+               [("f_u", C.c_double), ("l_sca2", C.c_double), ("gpu_ms", C.c_double),
+                ("kernel_launches", C.c_int64), ("march_ms", C.c_double), ("march_launches", C.c_int64),
+                ("jsca_pixels", C.c_int64)]
+
+    def to_dict(self, n_lambda=1):
+        out = {}
+        for name, typ in self._fields_:
+            v = getattr(self, name)
+            out[name] = np.array(v[:n_lambda]) if hasattr(v, "__len__") else v
+        return out
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libdartray.so (building it first if asked and missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libdartray.so not built ({path}); run __graft_entry__.build()")
+        _build.build()
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "dartray_params_default": ([P], C.c_int),
+        "dartray_grid_create": ([P, P, P, P], C.c_int),
+        "dartray_direct": ([P, P], C.c_int),
+        "dartray_scatter_iter": ([P, P, P], C.c_int),
+        "dartray_rfed": ([P, P, P, C.c_int], C.c_int),
+        "dartray_jsca_layout": ([P, P, P, P], C.c_int),
+        "dartray_jsca": ([P, C.c_int, P, C.c_int], C.c_int),
+        "dartray_map": ([P, P, C.c_int32, C.c_int32, C.c_int32, P, C.c_int], C.c_int),
+        "dartray_state_save": ([P, C.c_char_p], C.c_int),
+        "dartray_state_load": ([P, C.c_char_p], C.c_int),
+        "dartray_grid_destroy": ([P], None),
+        "dartray_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+EXPORTED = ("dartray_params_default", "dartray_grid_create", "dartray_direct", "dartray_scatter_iter",
+            "dartray_rfed", "dartray_jsca_layout", "dartray_jsca", "dartray_map", "dartray_state_save",
+            "dartray_state_load", "dartray_grid_destroy", "dartray_last_error")
+
+
+def _check(rc):
+    if rc != 0:
+        msg = load().dartray_last_error().decode(errors="replace")
+        raise DartRayError(rc, msg)
+
+
+# ---------------------------------------------------------------- raw calls
+def dartray_params_default():
+    p = dartray_params()
+    _check(load().dartray_params_default(C.byref(p)))
+    return p
+
+
+def dartray_grid_create(desc, params, stream=None):
+    h = C.c_void_p()
+    _check(load().dartray_grid_create(C.byref(desc), C.byref(params) if params is not None else None,
+                                      C.c_void_p(stream or 0), C.byref(h)))
+    return h
+
+
+def dartray_direct(h):
+    st = dartray_stats()
+    _check(load().dartray_direct(h, C.byref(st)))
+    return st
+
+
+def dartray_scatter_iter(h):
+    st = dartray_stats()
+    rem = C.c_double(0)
+    _check(load().dartray_scatter_iter(h, C.byref(rem), C.byref(st)))
+    return rem.value, st
+
+
+def dartray_rfed(h, U_ptr, Labs_ptr, dst_is_device):
+    _check(load().dartray_rfed(h, U_ptr, Labs_ptr, int(dst_is_device)))
+
+
+def dartray_jsca_layout(h, n_lambda):
+    k = (C.c_int32 * MAX_LAMBDA)()
+    off = (C.c_int64 * MAX_LAMBDA)()
+    tot = C.c_int64()
+    _check(load().dartray_jsca_layout(h, k, off, C.byref(tot)))
+    return list(k[:n_lambda]), list(off[:n_lambda]), tot.value
+
+
+def dartray_jsca(h, which, out_ptr, dst_is_device):
+    _check(load().dartray_jsca(h, int(which), out_ptr, int(dst_is_device)))
+
+
+def dartray_map(h, observer, nside_k, max_sub, use_jsca, out_ptr, dst_is_device):
+    obs = (C.c_double * 3)(*[float(v) for v in observer])
+    _check(load().dartray_map(h, obs, int(nside_k), int(max_sub), int(use_jsca), out_ptr, int(dst_is_device)))
+
+
+def dartray_state_save(h, path):
+    _check(load().dartray_state_save(h, os.fsencode(path)))
+
+
+def dartray_state_load(h, path):
+    _check(load().dartray_state_load(h, os.fsencode(path)))
+
+
+def dartray_grid_destroy(h):
+    load().dartray_grid_destroy(h)
+
+
+# ---------------------------------------------------------------- helpers
+def _is_cuda_tensor(x):
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_cuda_tensor(x):
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return C.c_void_p(x.ctypes.data) if x.size else None
+    raise TypeError(type(x))
+
+
+def default_params(**overrides):
+    p = dartray_params_default()
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class DartRay:
+    """One grid on the current CUDA device.
+
+    ``grid`` is a synth.Grid-like object (nroot, root_lo, root_size,
+    first_child, leaf_of_node, kappa_rho, emissivity, albedo, g, point_xyz,
+    point_lum).  Arrays may be numpy (host) or CUDA tensors (then all of them
+    must be, and ``inputs_on_device`` is set).
+    """
+
+    def __init__(self, grid, stream=None, **params):
+        self.grid = grid
+        self.n_leaf = int(grid.n_leaf)
+        self.n_lambda = int(grid.n_lambda)
+        self.params = default_params(**params)
+        fields = dict(first_child=grid.first_child, leaf_of_node=grid.leaf_of_node, kappa_rho=grid.kappa_rho,
+                      emissivity=grid.emissivity, albedo=grid.albedo, g=grid.g, point_xyz=grid.point_xyz,
+                      point_lum=grid.point_lum)
+        on_dev = _is_cuda_tensor(grid.kappa_rho)
+        keep = {}
+        for k, v in fields.items():
+            if on_dev:
+                keep[k] = v.contiguous()
+            else:
+                dt = np.int32 if k in ("first_child", "leaf_of_node") else np.float32
+                keep[k] = np.ascontiguousarray(v, dt)
+        self._keep = keep
+        d = dartray_grid_desc()
+        d.nroot[:] = [int(v) for v in grid.nroot]
+        d.root_lo[:] = [float(v) for v in grid.root_lo]
+        d.root_size = float(grid.root_size)
+        d.n_nodes = int(keep["first_child"].shape[0])
+        d.n_leaf = self.n_leaf
+        d.n_lambda = self.n_lambda
+        for k in fields:
+            setattr(d, k, _ptr(keep[k]).value if _ptr(keep[k]) is not None else None)
+        d.n_point = int(keep["point_xyz"].shape[0])
+        d.inputs_on_device = 1 if on_dev else 0
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                stream = None
+        self.stream = stream
+        self._h = dartray_grid_create(d, self.params, stream)
+        self.k_lam, self.off_lam, self.sca_len = dartray_jsca_layout(self._h, self.n_lambda)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            dartray_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def direct(self):
+        return dartray_direct(self._h).to_dict(self.n_lambda)
+
+    def scatter_iter(self):
+        rem, st = dartray_scatter_iter(self._h)
+        return rem, st.to_dict(self.n_lambda)
+
+    def rfed(self, U=None, L_abs=None):
+        dev = _is_cuda_tensor(U) or _is_cuda_tensor(L_abs)
+        if U is None and not dev:
+            U = np.empty((self.n_leaf, self.n_lambda), np.float32)
+        if L_abs is None and not dev:
+            L_abs = np.empty((self.n_leaf, self.n_lambda), np.float32)
+        dartray_rfed(self._h, _ptr(U), _ptr(L_abs), dev)
+        return U, L_abs
+
+    def jsca(self, which="total", out=None):
+        dev = _is_cuda_tensor(out)
+        if out is None:
+            out = np.empty(self.sca_len, np.float32)
+        dartray_jsca(self._h, 0 if which == "total" else 1, _ptr(out), dev)
+        return out
+
+    def jsca_block(self, l, which="total"):
+        a = self.jsca(which)
+        npx = 12 * 4 ** self.k_lam[l]
+        return a[self.off_lam[l]: self.off_lam[l] + self.n_leaf * npx].reshape(self.n_leaf, npx)
+
+    def map(self, observer, nside_k, max_sub=4, use_jsca=True, out=None):
+        dev = _is_cuda_tensor(out)
+        if out is None:
+            out = np.empty((self.n_lambda, 12 * 4 ** nside_k), np.float32)
+        dartray_map(self._h, observer, nside_k, max_sub, use_jsca, _ptr(out), dev)
+        return out
+
+    def save(self, path):
+        dartray_state_save(self._h, path)
+
+    def load(self, path):
+        dartray_state_load(self._h, path)

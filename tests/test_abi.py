@@ -1,0 +1,107 @@
+"""The C-ABI library loads, exports every call include/dartray.h declares, and
+rejects bad grid descriptions on the host before touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1709_03802_gb300 as pkg
+import synth
+from paper_1709_03802_gb300 import dartray as dr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_calls():
+    with open(os.path.join(ROOT, "include", "dartray.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dartray_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_call():
+    lib = pkg.load()
+    names = declared_calls()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(pkg.EXPORTED)
+
+
+def test_params_default():
+    p = pkg.dartray_params_default()
+    assert p.a_rt == 0.05 and p.n_rays_min == 5 and p.n_rays_max == 40 and p.k0 == 2
+    assert p.n_fwhm == 5 and p.k_sca_cap == 3 and p.merge == 1 and p.src_stride == 1
+
+
+def _desc(grid, **over):
+    keep = dict(fc=np.ascontiguousarray(grid.first_child, np.int32),
+                lon=np.ascontiguousarray(grid.leaf_of_node, np.int32),
+                kr=np.ascontiguousarray(grid.kappa_rho, np.float32),
+                em=np.ascontiguousarray(grid.emissivity, np.float32),
+                al=np.ascontiguousarray(grid.albedo, np.float32), g=np.ascontiguousarray(grid.g, np.float32))
+    keep.update(over)
+    d = dr.dartray_grid_desc()
+    d.nroot[:] = grid.nroot
+    d.root_lo[:] = grid.root_lo
+    d.root_size = grid.root_size
+    d.n_nodes = keep["fc"].shape[0]
+    d.n_leaf = grid.n_leaf
+    d.n_lambda = grid.n_lambda
+    d.first_child = keep["fc"].ctypes.data
+    d.leaf_of_node = keep["lon"].ctypes.data
+    d.kappa_rho = keep["kr"].ctypes.data
+    d.emissivity = keep["em"].ctypes.data
+    d.albedo = keep["al"].ctypes.data
+    d.g = keep["g"].ctypes.data
+    return d, keep
+
+
+def _create(d):
+    lib = pkg.load()
+    h = C.c_void_p()
+    rc = lib.dartray_grid_create(C.byref(d), None, None, C.byref(h))
+    return rc, lib.dartray_last_error().decode()
+
+
+def test_rejects_cyclic_tree():
+    grid = synth.config1(as_tree=True)
+    fc = np.ascontiguousarray(grid.first_child, np.int32).copy()
+    fc[9] = 1  # a child pointing back into the tree
+    d, keep = _desc(grid, fc=fc)
+    rc, msg = _create(d)
+    assert rc == -1 and msg
+
+
+def test_rejects_bad_leaf_ids():
+    grid = synth.config1()
+    lon = np.ascontiguousarray(grid.leaf_of_node, np.int32).copy()
+    lon[5] = lon[6]
+    d, keep = _desc(grid, lon=lon)
+    rc, msg = _create(d)
+    assert rc == -1 and "leaf" in msg
+
+
+def test_rejects_inexact_coordinates():
+    grid = synth.config1()
+    d, keep = _desc(grid)
+    d.root_size = 2.0 / 9.0
+    rc, msg = _create(d)
+    assert rc == -1 and "exact" in msg
+
+
+def test_rejects_bad_albedo():
+    grid = synth.config1()
+    d, keep = _desc(grid, al=np.array([1.5], np.float32))
+    rc, msg = _create(d)
+    assert rc == -1
+
+
+def test_rejects_unsupported_lambda_count():
+    grid = synth.config1()
+    d, keep = _desc(grid)
+    d.n_lambda = 3
+    rc, msg = _create(d)
+    assert rc == -1 and "n_lambda" in msg

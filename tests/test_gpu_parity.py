@@ -1,0 +1,212 @@
+"""Parity of the CUDA sweep (through the C ABI) with the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (floating point, float32 GPU vs float64 oracle): per-cell RFED
+<= 1e-3 relative for cells above 1e-6 of the maximum; total absorbed,
+scattered and escaped luminosity <= 1e-4 relative; crossing, split, block and
+merge counts within 1e-4 relative (at least 2 events, for small counts: a
+float32 distance can flip one decision that sits on its threshold)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1709_03802_gb300 import DartRay, DartRayError  # noqa: E402
+
+REL_CELL = 1e-3
+REL_TOTAL = 1e-4
+
+
+def close_counts(a, b, rel=1e-4, floor=2):
+    return abs(a - b) <= max(rel * max(a, b), floor)
+
+
+def check_rfed(gpu, ref, tag=""):
+    U, L_abs = gpu.rfed()
+    Ur, Lr = ref.rfed()
+    big = Ur > 1e-6 * Ur.max()
+    rel = np.abs(U[big] / Ur[big] - 1)
+    assert rel.max() <= REL_CELL, f"{tag} per-cell U rel {rel.max():.3e}"
+    # cells below the floor are still small on both sides
+    assert np.all(np.abs(U[~big]) <= 2e-6 * Ur.max() + 1e-30)
+    assert abs(L_abs.sum() / Lr.sum() - 1) <= REL_TOTAL
+    return rel.max()
+
+
+def check_ledger(st, ref, tag=""):
+    led, cnt = ref.stats()
+    for k in ("emitted", "absorbed", "scattered", "escaped", "blocked", "cut"):
+        a, b = np.asarray(st[k]), led[k]
+        tot = led["emitted"].sum()
+        assert np.all(np.abs(a - b) <= REL_TOTAL * max(tot, 1e-300)), f"{tag} ledger {k}: {a} vs {b}"
+    for k in ("crossings", "rays", "splits", "blocks", "escapes", "cuts", "lows", "merges"):
+        assert close_counts(st[k], cnt[k]), f"{tag} count {k}: {st[k]} vs {cnt[k]}"
+
+
+def run_pair(grid, n_iter, **params):
+    gpu = DartRay(grid, **params)
+    ref = oracle.Oracle(grid, oracle.OracleParams(**params))
+    st = gpu.direct()
+    ref.direct()
+    check_ledger(st, ref, "direct")
+    check_rfed(gpu, ref, "direct")
+    assert abs(st["f_u"] - ref.f_u) <= 1e-12 * max(ref.f_u, 1e-300)
+    for it in range(n_iter):
+        rem, st = gpu.scatter_iter()
+        rem_ref = ref.scatter_iter()
+        check_ledger(st, ref, f"iter{it}")
+        check_rfed(gpu, ref, f"iter{it}")
+        assert abs(rem - rem_ref) <= REL_TOTAL * max(rem_ref, 1e-12)
+    return gpu, ref
+
+
+def test_sphere_direct_and_scattering():
+    grid = synth.small_sphere(9, cell=0.25, radius=0.8, tau_radial=1.0)
+    gpu, ref = run_pair(grid, 2, a_rt=0.05, r_pre=0.5)
+    # scattering source function, per pixel
+    for which in ("total", "pending"):
+        a = gpu.jsca_block(0, which)
+        b = ref.jsca(0, which)
+        big = b > 1e-6 * b.max()
+        assert np.abs(a[big] / b[big] - 1).max() <= REL_CELL
+
+
+def test_config1_full():
+    """16^3 sphere, one source, direct light + 3 scattering iterations."""
+    grid = synth.config1()
+    run_pair(grid, 3, a_rt=0.05, r_pre=0.3)
+
+
+def test_tree_representation():
+    grid = synth.config1(as_tree=True)
+    run_pair(grid, 1, a_rt=0.05, r_pre=0.3)
+
+
+@pytest.mark.parametrize("merge", [0, 1])
+def test_adaptive_galaxy(merge):
+    grid = synth.galaxy_disk(max_level=3, threshold=0.3, nroot=(3, 3, 1), root_size=4.0)
+    gpu, ref = run_pair(grid, 1, a_rt=0.05, r_pre=2.0, merge=merge, src_stride=23)
+    if merge:
+        assert ref.stats()[1]["merges"] >= 0
+
+
+def test_multi_lambda():
+    g1 = synth.small_sphere(7, cell=0.25, radius=0.7, tau_radial=1.0)
+    nl = 4
+    kr = g1.kappa_rho * np.array([1.6, 1.0, 0.6, 0.3], np.float32)[None, :]
+    em = np.repeat(g1.emissivity, nl, axis=1) * np.array([0.5, 1.0, 1.0, 0.7], np.float32)[None, :]
+    grid = g1.with_lambda(kr, em, [0.7, 0.6, 0.5, 0.4], [0.75, 0.6, 0.5, 0.4])
+    run_pair(grid, 1, a_rt=0.05, r_pre=0.4)
+
+
+def test_point_sources():
+    g = synth.lognormal_cube(8, 4, n_src=3, tau_mean=1.5)
+    pts = np.array([[0.13, -0.27, 0.41], [-0.6, 0.2, -0.05]], np.float32)
+    grid = synth.Grid(nroot=g.nroot, root_lo=g.root_lo, root_size=g.root_size, first_child=g.first_child,
+                      leaf_of_node=g.leaf_of_node, leaf_lo=g.leaf_lo, leaf_size=g.leaf_size,
+                      kappa_rho=g.kappa_rho, emissivity=g.emissivity, albedo=g.albedo, g=g.g,
+                      point_xyz=pts, point_lum=np.array([[0.5], [0.25]], np.float32))
+    run_pair(grid, 1, a_rt=0.02, r_pre=0.6)
+
+
+def test_no_sources_gives_zero():
+    grid = synth.config1()
+    grid.emissivity[:] = 0
+    gpu = DartRay(grid)
+    st = gpu.direct()
+    U, L = gpu.rfed()
+    assert st["sources"] == 0 and st["crossings"] == 0 and np.all(U == 0)
+    rem, st = gpu.scatter_iter()
+    assert rem == 0 and st["crossings"] == 0
+
+
+def test_single_cell_model():
+    grid = synth.sphere_cube(1, radius=10.0, tau_radial=5.0)
+    run_pair(grid, 1, a_rt=0.05, r_pre=1.0)
+
+
+def test_scatter_before_direct_is_an_error():
+    gpu = DartRay(synth.config1())
+    with pytest.raises(DartRayError) as e:
+        gpu.scatter_iter()
+    assert e.value.code == -6
+
+
+def test_crossing_cap_reports_limit():
+    gpu = DartRay(synth.config1(), max_cross=3)
+    with pytest.raises(DartRayError) as e:
+        gpu.direct()
+    assert e.value.code == -5
+    # the grid stays usable
+    gpu2 = DartRay(synth.config1())
+    gpu2.direct()
+
+
+def test_small_queues_recover_by_batching():
+    grid = synth.galaxy_disk(max_level=2, threshold=0.3, nroot=(3, 3, 1), root_size=4.0)
+    a = DartRay(grid, queue_rays=1 << 16, r_pre=2.0)
+    b = DartRay(grid, r_pre=2.0)
+    sa, sb = a.direct(), b.direct()
+    Ua, Ub = a.rfed()[0], b.rfed()[0]
+    assert sa["crossings"] == sb["crossings"]
+    assert np.abs(Ua - Ub).max() <= 1e-5 * Ub.max()
+
+
+def test_device_buffers_and_state_roundtrip(tmp_path):
+    grid = synth.small_sphere(7, cell=0.25, radius=0.6, tau_radial=1.0)
+    gpu = DartRay(grid, r_pre=0.4)
+    gpu.direct()
+    gpu.scatter_iter()
+    U_dev = torch.empty((grid.n_leaf, 1), dtype=torch.float32, device="cuda")
+    gpu.rfed(U=U_dev)
+    U_host, _ = gpu.rfed()
+    assert np.array_equal(U_dev.cpu().numpy(), U_host)
+    path = str(tmp_path / "state.bin")
+    gpu.save(path)
+    m1 = gpu.map([0.05, -0.1, 0.02], 3)
+    other = DartRay(grid, r_pre=0.4)
+    other.load(path)
+    assert np.array_equal(other.rfed()[0], U_host)
+    m2 = other.map([0.05, -0.1, 0.02], 3)
+    assert np.abs(m2 - m1).max() <= 1e-6 * m1.max()  # float atomics: order may differ
+
+
+def test_inputs_on_device():
+    grid = synth.small_sphere(7, cell=0.25, radius=0.6, tau_radial=1.0)
+    import dataclasses
+    dgrid = dataclasses.replace(
+        grid, first_child=torch.from_numpy(grid.first_child).cuda(),
+        leaf_of_node=torch.from_numpy(grid.leaf_of_node).cuda(),
+        kappa_rho=torch.from_numpy(grid.kappa_rho).cuda(), emissivity=torch.from_numpy(grid.emissivity).cuda(),
+        albedo=torch.from_numpy(grid.albedo).cuda(), g=torch.from_numpy(grid.g).cuda(),
+        point_xyz=torch.zeros((0, 3), device="cuda"), point_lum=torch.zeros((0, 1), device="cuda"))
+    a = DartRay(dgrid, r_pre=0.4)
+    b = DartRay(grid, r_pre=0.4)
+    a.direct()
+    b.direct()
+    assert np.array_equal(a.rfed()[0], b.rfed()[0]) or np.abs(a.rfed()[0] - b.rfed()[0]).max() < 1e-6 * b.rfed()[0].max()
+
+
+@pytest.mark.parametrize("use_jsca", [0, 1])
+def test_map_parity(use_jsca):
+    grid = synth.small_sphere(9, cell=0.25, radius=0.8, tau_radial=1.0)
+    params = dict(a_rt=0.05, r_pre=0.5)
+    gpu = DartRay(grid, **params)
+    ref = oracle.Oracle(grid, oracle.OracleParams(**params))
+    gpu.direct()
+    ref.direct()
+    gpu.scatter_iter()
+    ref.scatter_iter()
+    obs = [0.3, -0.2, 0.1]
+    a = gpu.map(obs, 3, max_sub=3, use_jsca=bool(use_jsca))
+    b = ref.map(obs, 3, max_sub=3, use_jsca=bool(use_jsca))
+    big = b > 1e-6 * b.max()
+    assert np.abs(a[big] / b[big] - 1).max() <= REL_CELL
+    assert abs(a.sum() / b.sum() - 1) <= REL_TOTAL
