@@ -108,10 +108,13 @@ typedef struct dartray_params {
     int32_t max_waves;    /* waves per source batch before DARTRAY_E_LIMIT (200) */
     int32_t src_stride;   /* process sources s with s % src_stride == src_offset (1) */
     int32_t src_offset;   /* (0) */
-    int64_t queue_rays;   /* capacity of each ray queue, records (1 << 24) */
-    int64_t src_batch;    /* sources traced together; 0 = all (0) */
+    int64_t queue_rays;   /* capacity of each ray queue, records; 0 = automatic (0) */
+    int64_t src_batch;    /* upper bound on sources traced together; 0 = automatic (0) */
     int32_t profile;      /* 1: time every ray-march launch with CUDA events (0) */
-    int32_t reserved;
+    int32_t deposit_direct; /* 1: deposit j_sca with per-pixel atomics only (0: deferred
+                               per-cell accumulation of crossing records, atomics only
+                               when the record buffer is full) */
+    int64_t deposit_records; /* record buffer capacity; 0 = automatic (0) */
 } dartray_params;
 
 /* Per-call statistics.  Ledger entries are luminosities per wavelength of the

@@ -70,6 +70,7 @@ struct dartray_grid {
     // device arrays
     int32_t *d_node_child = nullptr, *d_rope = nullptr;
     float4 *d_node_box = nullptr, *d_leaf_box = nullptr, *d_dirtab = nullptr;
+    float *d_ztab = nullptr;
     float *d_kr = nullptr, *d_emis = nullptr, *d_pxyz = nullptr, *d_plum = nullptr;
     float *d_U = nullptr, *d_ULL = nullptr, *d_pend[2] = {nullptr, nullptr}, *d_jtot = nullptr;
     int cur = 0;  // d_pend[cur]: luminosity to emit; d_pend[1-cur]: deposit target
@@ -98,6 +99,12 @@ struct dartray_grid {
     int num_sms = 1;
     int march_blocks = 1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // deferred deposit records
+    unsigned *d_rec_cell = nullptr, *d_srt_cell = nullptr, *d_cnt = nullptr, *d_off = nullptr, *d_cur = nullptr;
+    float4 *d_rec_dir = nullptr, *d_srt_dir = nullptr;
+    float *d_rec_coef = nullptr, *d_srt_coef = nullptr;
+    unsigned long long *d_rec_n = nullptr;
+    long long rec_cap = 0;
     cudaEvent_t mev0 = nullptr, mev1 = nullptr;  // around each march launch (profile mode)
     double march_ms = 0.0;
     long long march_launches = 0;
@@ -106,11 +113,13 @@ struct dartray_grid {
 namespace {
 
 void free_all(dartray_grid *g) {
-    void *ptrs[] = {g->d_node_child, g->d_rope, g->d_node_box, g->d_leaf_box, g->d_dirtab, g->d_kr, g->d_emis,
+    void *ptrs[] = {g->d_ztab, g->d_node_child, g->d_rope, g->d_node_box, g->d_leaf_box, g->d_dirtab, g->d_kr, g->d_emis,
                     g->d_pxyz, g->d_plum, g->d_U, g->d_ULL, g->d_pend[0], g->d_pend[1], g->d_jtot, g->d_flags,
                     g->d_blocksum, g->d_total, g->d_src_idx, g->d_src_leaf, g->d_src_hint, g->d_src_pos,
                     g->d_src_S, g->d_H[0], g->d_H[1], g->d_M[0], g->d_M[1], g->d_L, g->d_HI[0], g->d_HI[1],
-                    g->d_MI[0], g->d_MI[1], g->d_LI, g->d_hkey, g->d_hcnt, g->d_hmem, g->d_wc, g->d_st, g->d_sum};
+                    g->d_MI[0], g->d_MI[1], g->d_LI, g->d_hkey, g->d_hcnt, g->d_hmem, g->d_wc, g->d_st, g->d_sum,
+                    g->d_rec_cell, g->d_srt_cell, g->d_cnt, g->d_off, g->d_cur, g->d_rec_dir, g->d_srt_dir, g->d_rec_coef,
+                    g->d_srt_coef, g->d_rec_n};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (g->ev0) cudaEventDestroy(g->ev0);
@@ -192,9 +201,43 @@ int build_sources(dartray_grid *g, int mode, const float *pend_src, int *n_src) 
     return DARTRAY_OK;
 }
 
+// Expand the buffered crossing records into the pending j_sca rows: bucket
+// the records by cell and let one warp accumulate each cell's row.
+int flush_records(dartray_grid *g, float *pend_dst) {
+    if (g->rec_cap == 0) return DARTRAY_OK;
+    unsigned long long n = 0;
+    CK(cudaMemcpyAsync(&n, g->d_rec_n, sizeof n, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (n == 0) return DARTRAY_OK;
+    const long long nr = std::min<long long>(static_cast<long long>(n), g->rec_cap);
+    cudaStream_t s = g->stream;
+    const int nb = (g->n_leaf + kBlock - 1) / kBlock;
+    const int gb = std::max(1, std::min<int>(static_cast<int>((nr + kBlock - 1) / kBlock), 8 * g->num_sms));
+    // per-cell counts were taken by the marcher
+    scan_blocks_kernel<<<nb, kBlock, 0, s>>>(reinterpret_cast<const int *>(g->d_cnt), g->n_leaf, g->d_blocksum);
+    scan_offsets_kernel<<<1, 1, 0, s>>>(g->d_blocksum, nb, g->d_total);
+    scan_apply_kernel<<<nb, kBlock, 0, s>>>(g->d_cnt, g->n_leaf, g->d_blocksum, g->d_off, g->d_cur);
+    rec_scatter_kernel<<<gb, kBlock, 0, s>>>(g->d_rec_cell, g->d_rec_dir, g->d_rec_coef, nr, g->rec_cap, g->nl,
+                                             g->d_cur, g->d_srt_cell, g->d_srt_dir, g->d_srt_coef);
+    for (int l = 0; l < g->nl; ++l) {
+        const unsigned gbl = static_cast<unsigned>(8 * g->num_sms);
+        switch (g->k_lam[l]) {
+        case 0: cell_accumulate_kernel<1><<<gbl, kBlock, 0, s>>>(g->G, l, nr, g->d_srt_cell, g->d_srt_dir, g->d_srt_coef, g->rec_cap, pend_dst); break;
+        case 1: cell_accumulate_kernel<2><<<gbl, kBlock, 0, s>>>(g->G, l, nr, g->d_srt_cell, g->d_srt_dir, g->d_srt_coef, g->rec_cap, pend_dst); break;
+        case 2: cell_accumulate_kernel<6><<<gbl, kBlock, 0, s>>>(g->G, l, nr, g->d_srt_cell, g->d_srt_dir, g->d_srt_coef, g->rec_cap, pend_dst); break;
+        default: cell_accumulate_kernel<24><<<gbl, kBlock, 0, s>>>(g->G, l, nr, g->d_srt_cell, g->d_srt_dir, g->d_srt_coef, g->rec_cap, pend_dst); break;
+        }
+    }
+    g->launches += 4 + g->nl;
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(g->d_rec_n, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(g->d_cnt, 0, static_cast<size_t>(g->n_leaf) * sizeof(unsigned), s));
+    return DARTRAY_OK;
+}
+
 // Waves of one batch of sources [src_lo, src_lo + nb_src).
 int run_batch(dartray_grid *g, int mode, MarchArgs base, int src_lo, int nb_src, int kstart, int *status,
-              long long *waves) {
+              long long *waves, long long *peak) {
     long long nA = static_cast<long long>(nb_src) * (12ll << (2 * kstart));
     long long nB = 0;
     int wave_kind = 0, par = 0;
@@ -202,6 +245,7 @@ int run_batch(dartray_grid *g, int mode, MarchArgs base, int src_lo, int nb_src,
     for (int w = 0;; ++w) {
         if (nA + nB == 0) break;
         if (w >= g->P.max_waves) return fail(DARTRAY_E_LIMIT, "wave cap reached");
+        *peak = std::max(*peak, nA + nB);
         CK(cudaMemsetAsync(g->d_wc, 0, sizeof(WaveCounters), g->stream));
         MarchArgs A = base;
         A.wave_kind = wave_kind;
@@ -230,6 +274,15 @@ int run_batch(dartray_grid *g, int mode, MarchArgs base, int src_lo, int nb_src,
             g->march_ms += ms;
         }
         if (wc.status & ST_QUEUE) { *status = ST_QUEUE; return DARTRAY_OK; }
+        if (mode != MODE_LL && g->rec_cap > 0) {
+            unsigned long long nrec = 0;
+            CK(cudaMemcpyAsync(&nrec, g->d_rec_n, sizeof nrec, cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            if (static_cast<long long>(nrec) >= g->rec_cap / 2) {
+                int rcf = flush_records(g, base.pend_dst);
+                if (rcf) return rcf;
+            }
+        }
         if (wc.status & ST_CROSS_CAP) {
             char m[256];
             std::snprintf(m, sizeof m,
@@ -319,13 +372,28 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
     base.c_light = static_cast<float>(g->P.c_light);
     base.split_c = 4.0 * kPi * static_cast<double>(g->P.n_rays_min);
     base.merge_c = 4.0 * kPi * static_cast<double>(g->P.n_rays_max);
+    base.split_cf = static_cast<float>(base.split_c);
+    base.merge_cf = static_cast<float>(base.merge_c);
     base.k_ray_max = g->P.k_ray_max;
     base.merge = g->P.merge;
     base.max_cross = g->P.max_cross;
     base.wc = g->d_wc;
     base.st = g->d_st;
+    base.rec_cell = g->d_rec_cell;
+    base.rec_dir = g->d_rec_dir;
+    base.rec_coef = g->d_rec_coef;
+    base.rec_n = g->d_rec_n;
+    base.rec_cnt = g->d_cnt;
+    base.rec_cap = g->rec_cap;
 
-    long long batch = g->P.src_batch > 0 ? g->P.src_batch : n_src;
+    // Sources are traced in batches (the phase is additive over sources and
+    // U_LL is fixed during a phase, so batching does not change the result).
+    // The batch size follows the peak rays per source of a wave seen so far,
+    // so that a wave fits the queues; an overflow restarts the phase with
+    // smaller batches.
+    const long long npix0 = 12ll << (2 * kstart);
+    long long batch_cap = g->P.src_batch > 0 ? g->P.src_batch : n_src;
+    double rays_per_src = static_cast<double>(npix0) * 16.0;  // first guess: growth 16x
     DevStats snap{};
     CK(cudaMemcpyAsync(&snap, g->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -342,17 +410,27 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
             }
             CK(cudaMemsetAsync(pend_dst, 0, g->sca_len * sizeof(float), s));
         }
+        if (g->rec_cap > 0) {
+            CK(cudaMemsetAsync(g->d_rec_n, 0, sizeof(unsigned long long), s));
+            CK(cudaMemsetAsync(g->d_cnt, 0, static_cast<size_t>(g->n_leaf) * sizeof(unsigned), s));
+        }
         DevStats fresh = snap;
         std::memset(fresh.ledger, 0, sizeof fresh.ledger);
         CK(cudaMemcpyAsync(g->d_st, &fresh, sizeof(DevStats), cudaMemcpyHostToDevice, s));
         long long waves = 0;
         bool overflow = false;
-        for (long long lo = 0; lo < n_src; lo += batch) {
-            const int nb = static_cast<int>(std::min<long long>(batch, n_src - lo));
+        long long failed_nb = 0;
+        for (long long lo = 0; lo < n_src;) {
+            long long want = static_cast<long long>(0.8 * static_cast<double>(g->cap) / rays_per_src);
+            want = std::max<long long>(1, std::min(want, batch_cap));
+            const int nb = static_cast<int>(std::min<long long>(want, n_src - lo));
             int status = 0;
-            rc = run_batch(g, mode, base, static_cast<int>(lo), nb, kstart, &status, &waves);
+            long long peak = 0;
+            rc = run_batch(g, mode, base, static_cast<int>(lo), nb, kstart, &status, &waves, &peak);
             if (rc) return rc;
-            if (status == ST_QUEUE) { overflow = true; break; }
+            if (status == ST_QUEUE) { overflow = true; failed_nb = nb; break; }
+            rays_per_src = std::max(rays_per_src * 0.5, static_cast<double>(peak) / nb);
+            lo += nb;
         }
         if (!overflow) {
             DevStats out{};
@@ -365,12 +443,15 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
             std::memcpy(res->cnt, out.cnt, sizeof res->cnt);
             break;
         }
-        if (batch <= 1) return fail(DARTRAY_E_QUEUE, "ray queues overflow with a single source");
-        batch = std::max<long long>(1, batch / 4);
+        if (failed_nb <= 1) return fail(DARTRAY_E_QUEUE, "ray queues overflow with a single source");
+        batch_cap = std::max<long long>(1, failed_nb / 4);
+        rays_per_src = std::max(rays_per_src, 0.8 * static_cast<double>(g->cap) / batch_cap);
     }
     res->f_u = f_u;
     res->pend_sum = 0.0;
     if (mode != MODE_LL) {
+        rc = flush_records(g, pend_dst);
+        if (rc) return rc;
         CK(cudaMemsetAsync(g->d_sum, 0, sizeof(double), s));
         accumulate_pending_kernel<<<4 * g->num_sms, kBlock, 0, s>>>(pend_dst, g->d_jtot, g->sca_len, g->d_sum);
         ++g->launches;
@@ -439,9 +520,11 @@ int dartray_params_default(dartray_params *p) {
     p->max_waves = 200;
     p->src_stride = 1;
     p->src_offset = 0;
-    p->queue_rays = 1ll << 24;
+    p->queue_rays = 0;
     p->src_batch = 0;
     p->profile = 0;
+    p->deposit_direct = 0;
+    p->deposit_records = 0;
     return DARTRAY_OK;
 }
 
@@ -459,7 +542,8 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
     if (desc->n_leaf < 1 || desc->n_nodes < 1 || desc->n_point < 0) return fail(DARTRAY_E_INVAL, "bad sizes");
     if (P.k0 < 0 || P.k0 > 13 || P.k_ray_max < P.k0 || P.k_ray_max > 13 || P.k_sca_cap < 0 || P.k_sca_cap > 3 ||
         P.n_fwhm < 1 || P.n_rays_min < 0 || P.n_rays_max < 0 || P.src_stride < 1 || P.src_offset < 0 ||
-        P.src_offset >= P.src_stride || P.max_cross < 1 || P.max_waves < 1 || P.queue_rays < 1024 ||
+        P.src_offset >= P.src_stride || P.max_cross < 1 || P.max_waves < 1 ||
+        (P.queue_rays != 0 && P.queue_rays < 1024) || P.deposit_records < 0 ||
         !(P.c_light > 0) || P.a_rt < 0)
         return fail(DARTRAY_E_INVAL, "invalid parameters");
     const bool on_dev = desc->inputs_on_device != 0;
@@ -508,7 +592,13 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
 
     const size_t nU = static_cast<size_t>(desc->n_leaf) * nl;
     const long long ndir = dir_tab_offset(kDirTabLevels + 1);
-    g->cap = P.queue_rays;
+    // automatic sizes: large enough for the biggest waves of galaxy-sized
+    // grids, small for small grids
+    g->cap = P.queue_rays > 0 ? P.queue_rays
+                              : std::min<long long>(1ll << 26, std::max<long long>(1ll << 20, 256ll * desc->n_leaf));
+    g->rec_cap = P.deposit_direct ? 0
+                 : (P.deposit_records > 0 ? P.deposit_records
+                                          : std::min<long long>(1ll << 27, std::max<long long>(1ll << 20, 512ll * desc->n_leaf)));
     g->hcap = 1;
     while (g->hcap < 2 * g->cap) g->hcap <<= 1;
     const int n_all = desc->n_leaf + desc->n_point;
@@ -524,6 +614,7 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
     AL(g->d_leaf_box, desc->n_leaf);
     AL(g->d_rope, static_cast<size_t>(desc->n_leaf) * 6);
     AL(g->d_dirtab, ndir);
+    AL(g->d_ztab, static_cast<size_t>(ndir) * nl);
     AL(g->d_kr, nU);
     AL(g->d_emis, nU);
     AL(g->d_pxyz, static_cast<size_t>(desc->n_point) * 3);
@@ -555,6 +646,18 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
     AL(g->d_wc, 1);
     AL(g->d_st, 1);
     AL(g->d_sum, 1);
+    if (g->rec_cap > 0) {
+        AL(g->d_rec_cell, g->rec_cap);
+        AL(g->d_srt_cell, g->rec_cap);
+        AL(g->d_rec_dir, g->rec_cap);
+        AL(g->d_srt_dir, g->rec_cap);
+        AL(g->d_rec_coef, static_cast<size_t>(g->rec_cap) * nl);
+        AL(g->d_srt_coef, static_cast<size_t>(g->rec_cap) * nl);
+        AL(g->d_cnt, desc->n_leaf);
+        AL(g->d_off, desc->n_leaf);
+        AL(g->d_cur, desc->n_leaf);
+        AL(g->d_rec_n, 1);
+    }
 #undef AL
     cudaStream_t s = g->stream;
     auto up = [&](auto *dst, const auto *src, size_t cnt) { return copy_in(dst, src, cnt, false, s); };
@@ -595,12 +698,16 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
     G.point_xyz = g->d_pxyz;
     G.point_lum = g->d_plum;
     G.dirtab = g->d_dirtab;
+    G.ztab = g->d_ztab;
+    G.n_dirtab = ndir;
     for (int l = 0; l < nl; ++l) {
         G.albedo[l] = alb[l];
         G.g[l] = gg[l];
         G.k_lam[l] = g->k_lam[l];
         G.off_lam[l] = g->off_lam[l];
     }
+    ztab_kernel<<<static_cast<unsigned>((ndir + kBlock - 1) / kBlock), kBlock, 0, s>>>(G, g->d_ztab, ndir);
+    ++g->launches;
     switch (nl) {
     case 1: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<1, MODE_SCATTER>), g->num_sms); break;
     case 2: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<2, MODE_SCATTER>), g->num_sms); break;

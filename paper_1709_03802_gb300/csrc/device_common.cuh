@@ -13,7 +13,7 @@ constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr double kPi = 3.14159265358979323846;
 // HEALPix levels whose pixel centres are tabulated (levels 0..kDirTabLevels)
-constexpr int kDirTabLevels = 9;
+constexpr int kDirTabLevels = 11;
 // first table entry of level k: sum_{j<k} 12*4^j = 4*(4^k - 1)
 __host__ __device__ inline int64_t dir_tab_offset(int k) { return 4 * ((int64_t(1) << (2 * k)) - 1); }
 
@@ -32,6 +32,8 @@ struct DevGrid {
     const float *point_xyz;     // [n_point][3]
     const float *point_lum;     // [n_point][nl]
     const float4 *dirtab;       // pixel centres for levels 0..kDirTabLevels
+    const float *ztab;          // [nl][n_dirtab] HG row sums per ray direction
+    long long n_dirtab;
     float albedo[kMaxLambda], g[kMaxLambda];
     int k_lam[kMaxLambda];
     long long off_lam[kMaxLambda];
@@ -162,15 +164,21 @@ __device__ inline uint64_t vec2pix_d(int k, double vx, double vy, double vz) {
     return uint64_t(face) * uint64_t(ns) * uint64_t(ns) + (spread_bits(ix) | (spread_bits(iy) << 1));
 }
 
+// Directions beyond the table (levels above kDirTabLevels; rare), kept out of
+// line so the marcher's code stays small.
+__device__ __noinline__ float3 ray_dir_computed(int k, uint64_t p) {
+    double v[3];
+    pix2vec_d(k, p, v);
+    return make_float3(static_cast<float>(v[0]), static_cast<float>(v[1]), static_cast<float>(v[2]));
+}
+
 // Ray direction (float32) of pixel p at level k: table up to kDirTabLevels.
 __device__ inline float3 ray_dir(const DevGrid &G, int k, uint64_t p) {
     if (k <= kDirTabLevels) {
         const float4 v = __ldg(&G.dirtab[dir_tab_offset(k) + static_cast<int64_t>(p)]);
         return make_float3(v.x, v.y, v.z);
     }
-    double v[3];
-    pix2vec_d(k, p, v);
-    return make_float3(static_cast<float>(v[0]), static_cast<float>(v[1]), static_cast<float>(v[2]));
+    return ray_dir_computed(k, p);
 }
 
 // ------------------------------------------------------------------ traversal

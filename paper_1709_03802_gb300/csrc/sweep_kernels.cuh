@@ -40,14 +40,22 @@ struct MarchArgs {
     float *pend_dst;
     float f_u, r_pre, c_light;
     double split_c, merge_c; // 4 pi N_rays, 4 pi N_rays^max
+    float split_cf, merge_cf;
     int k_ray_max, merge, max_cross;
     WaveCounters *wc;
     DevStats *st;
+    // deferred j_sca deposit: one record per depositing crossing (cell, ray
+    // direction, scattered luminosity / HG row sum per wavelength)
+    unsigned *rec_cell;
+    float4 *rec_dir;
+    float *rec_coef;              // [nl][rec_cap]
+    unsigned long long *rec_n;
+    unsigned *rec_cnt;            // records per cell (for the bucketing)
+    long long rec_cap;
 };
 
-__device__ inline float omega_of(int k) {
-    return static_cast<float>(4.0 * kPi / (12.0 * static_cast<double>(1ull << (2 * k))));
-}
+// beam solid angle 4 pi / (12 4^k), scaled exactly from float(pi/3)
+__device__ inline float omega_of(int k) { return ldexpf(static_cast<float>(kPi / 3.0), -2 * k); }
 
 // Warp-aggregated append: returns this lane's slot (valid only where want).
 __device__ inline unsigned long long warp_append(bool want, unsigned long long *counter, int lane) {
@@ -60,12 +68,43 @@ __device__ inline unsigned long long warp_append(bool want, unsigned long long *
     return base + __popc(m & ((1u << lane) - 1u));
 }
 
+// Luminosity ledger of a lane: float32 sums in registers (few wavelengths)
+// reduced in double across the warp once per launch, or (many wavelengths)
+// double atomics in shared memory per finished ray.
 template <int NL>
-__device__ inline void flush_ledger(double (*sh_led)[kMaxLambda], int slot, const float *v, float scale) {
+struct Ledger {
+    static constexpr bool kReg = NL <= 4;
+    float acc[kReg ? LG_N : 1][kReg ? NL : 1];
+    __device__ void init() {
 #pragma unroll
-    for (int l = 0; l < NL; ++l)
-        if (v[l] != 0.f) atomicAdd(&sh_led[slot][l], static_cast<double>(v[l]) * scale);
-}
+        for (int s = 0; s < (kReg ? LG_N : 1); ++s)
+#pragma unroll
+            for (int l = 0; l < (kReg ? NL : 1); ++l) acc[s][l] = 0.f;
+    }
+    __device__ void add(double (*sh)[kMaxLambda], int slot, const float *v, float scale) {
+        if constexpr (kReg) {
+#pragma unroll
+            for (int l = 0; l < NL; ++l) acc[slot][l] = fmaf(v[l], scale, acc[slot][l]);
+        } else {
+#pragma unroll
+            for (int l = 0; l < NL; ++l)
+                if (v[l] != 0.f) atomicAdd(&sh[slot][l], static_cast<double>(v[l] * scale));
+        }
+    }
+    __device__ void flush(double (*sh)[kMaxLambda], int lane) {
+        if constexpr (kReg) {
+#pragma unroll
+            for (int s = 0; s < LG_N; ++s)
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    double v = acc[s][l];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+                    if (lane == 0 && v != 0.0) atomicAdd(&sh[s][l], v);
+                }
+        }
+    }
+};
 
 /*
  * One wave of rays.  Persistent warps: each lane owns one ray and marches it
@@ -83,7 +122,7 @@ __device__ inline void flush_ledger(double (*sh_led)[kMaxLambda], int slot, cons
  *     pixel loop of each depositing lane.
  */
 template <int NL, int MODE>
-__global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const MarchArgs A) {
+__global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march_kernel(const DevGrid G, const MarchArgs A) {
     __shared__ float4 sh_pix[kPixTab];
     __shared__ double sh_led[LG_N][kMaxLambda];
     __shared__ unsigned long long sh_cnt[CT_N];
@@ -111,11 +150,15 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
     float3 xs = make_float3(0, 0, 0), n = make_float3(0, 0, 1);
     float d = 0.f, supp = 0.f, omega_k = 0.f, entry_coord = 0.f;
     float4 box = make_float4(0, 0, 0, 0);
-    bool first = true;
+    float3 inv = make_float3(0, 0, 0);
+    bool first = true, dyadic_src = true, need_z = false;
     float I[NL], Z[NL], acc_dep[NL], acc_skip[NL];
+    float kr[NL], ull[NL];  // kappa*rho and U_LL of the current leaf (loaded with its box)
 #pragma unroll
     for (int l = 0; l < NL; ++l) { I[l] = 0.f; Z[l] = 1.f; acc_dep[l] = 0.f; acc_skip[l] = 0.f; }
     unsigned c_rays = 0, c_cross = 0, c_split = 0, c_block = 0, c_escape = 0, c_cut = 0, c_low = 0;
+    Ledger<NL> led;
+    led.init();
     unsigned long long c_jpix = 0;  // j_sca pixels updated (lane 0 of each warp counts)
 
     for (;;) {
@@ -136,6 +179,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
                     int par_axis = -1;
                     float par_coord = 0.f;
                     unsigned long long par_pix = 0;
+                    int par_leaf = -1;
                     supp = 0.f;
                     entry_axis = -1;
                     entry_coord = 0.f;
@@ -149,6 +193,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
                             d = 0.f;
                             hint = A.src_hint[src];
                             const float om = omega_of(lev);
+                            float emit[NL];
 #pragma unroll
                             for (int l = 0; l < NL; ++l) {
                                 float s;
@@ -161,8 +206,9 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
                                     s = A.src_S[static_cast<long long>(src) * NL + l];
                                 }
                                 I[l] = s;
-                                if (s != 0.f) atomicAdd(&sh_led[LG_EMITTED][l], static_cast<double>(s) * om);
+                                emit[l] = s;
                             }
+                            led.add(sh_led, LG_EMITTED, emit, om);
                         } else {
                             const long long pi_ = idx >> 2;
                             const RayRec r = A.H_in[pi_];
@@ -174,6 +220,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
                             par_axis = rr_axis(r.meta);
                             par_coord = r.plane;
                             par_pix = r.pix;
+                            par_leaf = r.hint;  // the cell the parent split in
 #pragma unroll
                             for (int l = 0; l < NL; ++l) I[l] = A.H_in_I[l * A.cap + pi_];
                         }
@@ -197,8 +244,20 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
                     const float4 sp = A.src_pos[src];
                     xs = make_float3(sp.x, sp.y, sp.z);
                     srcleaf = A.src_leaf[src];
+                    dyadic_src = A.src_hint[src] >= 0;  // cell sources sit on the dyadic lattice
                     n = ray_dir(G, lev, pix);
+                    inv = make_float3(__frcp_rn(n.x), __frcp_rn(n.y), __frcp_rn(n.z));
                     omega_k = omega_of(lev);
+                    need_z = false;
+                    if (MODE != MODE_LL) {
+                        if (lev <= kDirTabLevels) {
+#pragma unroll
+                            for (int l = 0; l < NL; ++l)
+                                Z[l] = __ldg(&G.ztab[l * G.n_dirtab + dir_tab_offset(lev) + static_cast<long long>(pix)]);
+                        } else {
+                            need_z = true;
+                        }
+                    }
                     if (hint >= 0) {
                         leaf = hint;
                     } else {
@@ -217,9 +276,18 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
                                 entry_coord = par_coord;
                             }
                         }
-                        leaf = locate_root(G, p, n);
+                        // most children start in the cell their parent split in
+                        if (par_leaf >= 0 && inside_box(__ldg(&G.leaf_box[par_leaf]), p, n)) leaf = par_leaf;
+                        else leaf = locate_root(G, p, n);
                     }
-                    if (leaf >= 0) box = __ldg(&G.leaf_box[leaf]);
+                    if (leaf >= 0) {
+                        box = __ldg(&G.leaf_box[leaf]);
+#pragma unroll
+                        for (int l = 0; l < NL; ++l) {
+                            kr[l] = __ldg(&G.kappa_rho[static_cast<long long>(leaf) * NL + l]);
+                            ull[l] = MODE == MODE_LL ? 0.f : __ldg(&A.U_LL[static_cast<long long>(leaf) * NL + l]);
+                        }
+                    }
                     first = true;
                     ncross = 0;
                     ++c_rays;
@@ -230,7 +298,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
 
         // ------------------------------- HG normalisation of new rays (shared)
         if (MODE != MODE_LL) {
-            unsigned m = __ballot_sync(kFull, started);
+            unsigned m = __ballot_sync(kFull, started && need_z);
             while (m) {
                 const int j = __ffs(m) - 1;
                 m &= m - 1;
@@ -265,7 +333,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
                 float tmp[NL];
 #pragma unroll
                 for (int l = 0; l < NL; ++l) tmp[l] = I[l];
-                flush_ledger<NL>(sh_led, LG_ESCAPED, tmp, omega_k);
+                led.add(sh_led, LG_ESCAPED, tmp, omega_k);
                 ++c_escape;
                 outcome = 1;
             } else if (++ncross > A.max_cross) {
@@ -281,9 +349,11 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
                 bnd[0] = n.x > 0.f ? box.x + box.w : box.x;
                 bnd[1] = n.y > 0.f ? box.y + box.w : box.y;
                 bnd[2] = n.z > 0.f ? box.z + box.w : box.z;
-                const float tx = n.x != 0.f ? (bnd[0] - xs.x) / n.x : inf;
-                const float ty = n.y != 0.f ? (bnd[1] - xs.y) / n.y : inf;
-                const float tz = n.z != 0.f ? (bnd[2] - xs.z) / n.z : inf;
+                // reciprocal multiplies keep exact ties exact (equal offsets and
+                // equal direction components give bitwise-equal distances)
+                const float tx = n.x != 0.f ? (bnd[0] - xs.x) * inv.x : inf;
+                const float ty = n.y != 0.f ? (bnd[1] - xs.y) * inv.y : inf;
+                const float tz = n.z != 0.f ? (bnd[2] - xs.z) * inv.z : inf;
                 te = fminf(tx, fminf(ty, tz));
                 tie = (tx == te ? 1 : 0) | (ty == te ? 2 : 0) | (tz == te ? 4 : 0);
                 if (tie == 0) {  // non-finite direction: never expected, never indexed
@@ -292,59 +362,76 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
                 }
                 const float ds = fmaxf(te - d, 0.f);
                 const float L = box.w, V = L * L * L;
-                float fac[NL], T[NL], kr[NL];
+                float fac[NL], T[NL];
                 bool neg[NL];
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
-                    kr[l] = __ldg(&G.kappa_rho[static_cast<long long>(leaf) * NL + l]);
+                    // T = e^-dtau; fac = (1 - T)/dtau, the segment average of the
+                    // attenuation (series below dtau = 1/64, where 1 - T cancels)
                     const float dtau = kr[l] * ds;
-                    fac[l] = dtau > 0.f ? -expm1f(-dtau) / dtau : 1.f;
-                    T[l] = expf(-dtau);
+                    T[l] = __expf(-dtau);
+                    fac[l] = dtau < 0.015625f
+                                 ? fmaf(-0.5f * dtau, fmaf(-dtau * (1.f / 3.f), fmaf(-0.25f, dtau, 1.f), 1.f), 1.f)
+                                 : __fdividef(1.f - T[l], dtau);
                     neg[l] = false;
                 }
                 outcome = active ? 0 : 1;
                 if (outcome == 0 && leaf != srcleaf) {
-                    // exact (double, uncontracted) geometry of the beam tests
-                    const double Ld = static_cast<double>(L);
-                    const double hx = __dmul_rn(0.5, Ld);
-                    const double dx = __dsub_rn(__dadd_rn(static_cast<double>(box.x), hx), static_cast<double>(xs.x));
-                    const double dy = __dsub_rn(__dadd_rn(static_cast<double>(box.y), hx), static_cast<double>(xs.y));
-                    const double dz = __dsub_rn(__dadd_rn(static_cast<double>(box.z), hx), static_cast<double>(xs.z));
-                    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                    // offset of the cell centre from the source (exact in float32
+                    // for cell sources: dyadic coordinates)
+                    const float hx = 0.5f * L;
+                    const float dxf = (box.x + hx) - xs.x, dyf = (box.y + hx) - xs.y, dzf = (box.z + hx) - xs.z;
+                    const float r2f = fmaf(dzf, dzf, fmaf(dyf, dyf, dxf * dxf));
                     if (MODE == MODE_LL) {
                         if (d >= A.r_pre) {
                             float tmp[NL];
 #pragma unroll
                             for (int l = 0; l < NL; ++l) tmp[l] = I[l];
-                            flush_ledger<NL>(sh_led, LG_CUT, tmp, omega_k);
+                            led.add(sh_led, LG_CUT, tmp, omega_k);
                             ++c_cut;
                             outcome = 1;
                         }
                     } else {
-                        const float r2f = static_cast<float>(r2);
+                        // Eq. 1: negligible when <I>/(r^2 c) < f_U U_LL
                         bool all = true;
 #pragma unroll
                         for (int l = 0; l < NL; ++l) {
-                            const float dU = (I[l] * fac[l]) / (r2f * A.c_light);
-                            neg[l] = dU < A.f_u * __ldg(&A.U_LL[static_cast<long long>(leaf) * NL + l]);
+                            neg[l] = I[l] * fac[l] < A.f_u * ull[l] * (r2f * A.c_light);
                             all = all && neg[l];
                         }
                         if (all) {
                             float tmp[NL];
 #pragma unroll
                             for (int l = 0; l < NL; ++l) tmp[l] = I[l];
-                            flush_ledger<NL>(sh_led, LG_BLOCKED, tmp, omega_k);
+                            led.add(sh_led, LG_BLOCKED, tmp, omega_k);
                             ++c_block;
                             outcome = 1;
                         }
                     }
-                    if (outcome == 0) {
-                        const double beam = ldexp(12.0, 2 * lev);
-                        const double rhs = __dmul_rn(__dmul_rn(beam, Ld), Ld);
-                        if (!(first && kind == kMerged) && lev < A.k_ray_max && __dmul_rn(A.split_c, r2) > rhs) {
+                    const bool can_split = !(first && kind == kMerged) && lev < A.k_ray_max;
+                    const bool can_merge = A.merge && lev > 0 && !first && L != supp;
+                    if (outcome == 0 && (can_split || can_merge)) {
+                        // Eq. 2 / Eq. 3 as 4 pi N r^2 vs 12 4^k L^2.  float32 decides
+                        // unless within 1e-5 of the threshold (or the source is not
+                        // on the dyadic lattice); then the exact double comparison.
+                        const float rhs_f = ldexpf(12.f, 2 * lev) * L * L;
+                        const float ls = A.split_cf * r2f, lm = A.merge_cf * r2f;
+                        bool sp = ls > rhs_f, mg = lm < rhs_f;
+                        if (!dyadic_src || fabsf(ls - rhs_f) <= 1e-5f * rhs_f || fabsf(lm - rhs_f) <= 1e-5f * rhs_f) {
+                            const double Ld = static_cast<double>(L);
+                            const double hd = __dmul_rn(0.5, Ld);
+                            const double dx = __dsub_rn(__dadd_rn(static_cast<double>(box.x), hd), static_cast<double>(xs.x));
+                            const double dy = __dsub_rn(__dadd_rn(static_cast<double>(box.y), hd), static_cast<double>(xs.y));
+                            const double dz = __dsub_rn(__dadd_rn(static_cast<double>(box.z), hd), static_cast<double>(xs.z));
+                            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                            const double rhs = __dmul_rn(__dmul_rn(ldexp(12.0, 2 * lev), Ld), Ld);
+                            sp = __dmul_rn(A.split_c, r2) > rhs;
+                            mg = __dmul_rn(A.merge_c, r2) < rhs;
+                        }
+                        if (can_split && sp) {
                             outcome = 2;
                             ++c_split;
-                        } else if (A.merge && lev > 0 && !first && L != supp && __dmul_rn(A.merge_c, r2) < rhs) {
+                        } else if (can_merge && mg) {
                             outcome = 3;
                             ++c_low;
                         }
@@ -376,7 +463,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
             if (wh) {
                 if (slot < static_cast<unsigned long long>(A.cap)) {
                     RayRec r;
-                    r.pix = pix; r.src = src; r.d = d; r.hint = -1; r.supp = 0.f; r.plane = entry_coord;
+                    r.pix = pix; r.src = src; r.d = d; r.hint = leaf; r.supp = 0.f; r.plane = entry_coord;
                     r.meta = rr_meta(lev, kind, entry_axis);
                     A.H_out[slot] = r;
 #pragma unroll
@@ -401,12 +488,34 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
             }
         }
 
-        // ------------------------------- warp-cooperative j_sca deposit (Eq. 4)
+        // ------------------------------------------- j_sca deposit (Eq. 4)
+        // Deferred: a record per depositing crossing, expanded per cell later
+        // (cell_accumulate_kernel).  Lanes that find the record buffer full
+        // deposit directly, all 32 lanes sharing the pixel loop.
         if (MODE != MODE_LL) {
             bool has = false;
 #pragma unroll
             for (int l = 0; l < NL; ++l) has = has || (sca[l] > 0.f);
-            unsigned m = __ballot_sync(kFull, active && outcome == 0 && has);
+            has = has && active && outcome == 0;
+            bool direct_dep = false;
+            const unsigned long long rs = A.rec_cap > 0 ? warp_append(has, A.rec_n, lane) : 0ull;
+            if (has && A.rec_cap == 0) {
+                direct_dep = true;
+            } else if (has) {
+                if (rs < static_cast<unsigned long long>(A.rec_cap)) {
+                    atomicAdd(&A.rec_cnt[leaf], 1u);
+                    A.rec_cell[rs] = static_cast<unsigned>(leaf);
+                    A.rec_dir[rs] = make_float4(n.x, n.y, n.z, 0.f);
+#pragma unroll
+                    for (int l = 0; l < NL; ++l) {
+                        A.rec_coef[l * A.rec_cap + static_cast<long long>(rs)] = sca[l];
+                        if (sca[l] != 0.f) c_jpix += static_cast<unsigned>(npx[l]);
+                    }
+                } else {
+                    direct_dep = true;
+                }
+            }
+            unsigned m = __ballot_sync(kFull, direct_dep);
             while (m) {
                 const int j = __ffs(m) - 1;
                 m &= m - 1;
@@ -417,7 +526,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
                 for (int l = 0; l < NL; ++l) {
                     const float coef = __shfl_sync(kFull, sca[l], j);
                     if (coef == 0.f) continue;
-                    c_jpix += (lane == 0) ? static_cast<unsigned>(npx[l]) : 0u;
+                    c_jpix += (lane == j) ? static_cast<unsigned>(npx[l]) : 0u;
                     float *row = A.pend_dst + G.off_lam[l] + static_cast<long long>(lj) * npx[l];
                     for (int q = lane; q < npx[l]; q += kWarp) {
                         const float4 pd = sh_pix[pixbase[l] + q];
@@ -445,7 +554,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
                     float tmp[NL];
 #pragma unroll
                     for (int l = 0; l < NL; ++l) tmp[l] = I[l];
-                    flush_ledger<NL>(sh_led, LG_ESCAPED, tmp, omega_k);
+                    led.add(sh_led, LG_ESCAPED, tmp, omega_k);
                     ++c_escape;
                     outcome = 1;
                 } else if (nxt == leaf) {
@@ -454,13 +563,18 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
                 } else {
                     leaf = nxt;
                     box = __ldg(&G.leaf_box[leaf]);
+#pragma unroll
+                    for (int l = 0; l < NL; ++l) {
+                        kr[l] = __ldg(&G.kappa_rho[static_cast<long long>(leaf) * NL + l]);
+                        ull[l] = MODE == MODE_LL ? 0.f : __ldg(&A.U_LL[static_cast<long long>(leaf) * NL + l]);
+                    }
                     if (supp != 0.f && box.w != supp) supp = 0.f;
                     first = false;
                 }
             }
             if (outcome != 0) {
-                flush_ledger<NL>(sh_led, LG_DEPOSITED, acc_dep, 1.f);
-                flush_ledger<NL>(sh_led, LG_SKIPPED, acc_skip, 1.f);
+                led.add(sh_led, LG_DEPOSITED, acc_dep, 1.f);
+                led.add(sh_led, LG_SKIPPED, acc_skip, 1.f);
 #pragma unroll
                 for (int l = 0; l < NL; ++l) { acc_dep[l] = 0.f; acc_skip[l] = 0.f; }
                 active = false;
@@ -469,6 +583,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const DevGrid G, const Ma
     }
 
     // ---------------------------------------------------------- flush
+    led.flush(sh_led, lane);
     atomicAdd(&sh_cnt[CT_RAYS], static_cast<unsigned long long>(c_rays));
     atomicAdd(&sh_cnt[CT_CROSS], static_cast<unsigned long long>(c_cross));
     atomicAdd(&sh_cnt[CT_SPLIT], static_cast<unsigned long long>(c_split));
@@ -704,6 +819,27 @@ __global__ void accumulate_pending_kernel(const float *pend, float *total, long 
     }
 }
 
+// HG row normalisation per ray direction: Z[l][i] = sum_q (1 + g^2 -
+// 2 g n_q.n_i)^(-3/2) over the j_sca pixels of wavelength l, for every
+// tabulated ray direction i (levels 0..kDirTabLevels).
+__global__ void ztab_kernel(const DevGrid G, float *ztab, long long ndt) {
+    const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i >= ndt) return;
+    const float4 n = G.dirtab[i];
+    for (int l = 0; l < G.nl; ++l) {
+        const int k = G.k_lam[l], np = 12 << (2 * k);
+        const float B = 1.f + G.g[l] * G.g[l], Cg = 2.f * G.g[l];
+        const float4 *pd = G.dirtab + dir_tab_offset(k);
+        float z = 0.f;
+        for (int q = 0; q < np; ++q) {
+            const float4 v = pd[q];
+            const float r = rsqrtf(B - Cg * (v.x * n.x + v.y * n.y + v.z * n.z));
+            z += r * r * r;
+        }
+        ztab[l * ndt + i] = z;
+    }
+}
+
 // HEALPix pixel-centre table (levels 0..kDirTabLevels), computed in double.
 __global__ void dirtab_kernel(float4 *tab, long long n) {
     const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
@@ -722,6 +858,168 @@ __global__ void labs_kernel(const DevGrid G, const float *U, float c_light, floa
     const int leaf = static_cast<int>(i / G.nl), l = static_cast<int>(i % G.nl);
     const float L = G.leaf_box[leaf].w;
     L_abs[i] = (1.f - G.albedo[l]) * G.kappa_rho[i] * c_light * (L * L * L) * U[i];
+}
+
+// ------------------------------------------------------- deferred deposit
+// Records of depositing crossings are bucketed by cell (count, scan,
+// scatter) and each cell's scattering source-function row is accumulated by
+// one warp holding the row in registers: pending[c][q] += sum over records of
+// coef * Phi(n_q . n) / A, with Phi = A (1 + g^2 - 2 g mu)^(-3/2) (Eq. 4; the
+// constant A cancels against the row normalisation already in coef).
+__global__ void rec_count_kernel(const unsigned *cell, long long n, unsigned *cnt) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        atomicAdd(&cnt[cell[i]], 1u);
+}
+
+// exclusive scan of per-cell counts: block totals, then per-element offsets
+__global__ void scan_apply_kernel(const unsigned *cnt, int n, const int *block_off, unsigned *off, unsigned *cur) {
+    __shared__ unsigned sh[kBlock / kWarp];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned v = i < n ? cnt[i] : 0u;
+    unsigned incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) sh[w] = incl;
+    __syncthreads();
+    unsigned base = static_cast<unsigned>(block_off[blockIdx.x]);
+    for (int k = 0; k < w; ++k) base += sh[k];
+    if (i < n) {
+        off[i] = base + incl - v;
+        cur[i] = base + incl - v;
+    }
+}
+
+__global__ void rec_scatter_kernel(const unsigned *cell, const float4 *dir, const float *coef, long long n,
+                                   long long cap, int nl, unsigned *cur, unsigned *scell, float4 *sdir,
+                                   float *scoef) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const unsigned c = cell[i];
+        const unsigned pos = atomicAdd(&cur[c], 1u);
+        scell[pos] = c;
+        sdir[pos] = dir[i];
+        for (int l = 0; l < nl; ++l) scoef[l * cap + pos] = coef[l * cap + i];
+    }
+}
+
+constexpr int kAccRange = 2048;  // records per warp work unit
+
+// Packed single-precision pairs (sm_100+ f32x2): two IEEE fp32 operations per
+// instruction.
+__device__ __forceinline__ unsigned long long f2_pack(float2 a) {
+    unsigned long long u;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(u) : "f"(a.x), "f"(a.y));
+    return u;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long u) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(u));
+    return a;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Accumulate the records [beg, end) (sorted by cell) of wavelength l into the
+// pending rows; a row is flushed (with atomics: neighbouring ranges may share
+// the cell) whenever the cell changes.  Each lane owns PPL pixels, evaluated
+// in pairs: t = 1 + g^2 - 2g n_q.n, w = t^(-3/2), acc += coef w.
+template <int PPL>
+__device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, long long end, const unsigned *scell,
+                                        const float4 *sdir, const float *scoef, long long cap, float *pend,
+                                        int lane, float4 *sh_rec, unsigned *sh_cell) {
+    constexpr int NP2 = (PPL + 1) / 2;
+    const int k = G.k_lam[l];
+    const int np = 12 << (2 * k);
+    const float B = 1.f + G.g[l] * G.g[l], Cg = 2.f * G.g[l];
+    unsigned long long mx[NP2], my[NP2], mz[NP2], acc[NP2];  // minus pixel directions, sums
+#pragma unroll
+    for (int i = 0; i < NP2; ++i) {
+        float2 vx, vy, vz;
+        const int q0 = lane + kWarp * (2 * i), q1 = lane + kWarp * (2 * i + 1);
+        const float4 a = q0 < np ? __ldg(&G.dirtab[dir_tab_offset(k) + q0]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = q1 < np ? __ldg(&G.dirtab[dir_tab_offset(k) + q1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        vx = make_float2(-a.x, -b.x);
+        vy = make_float2(-a.y, -b.y);
+        vz = make_float2(-a.z, -b.z);
+        mx[i] = f2_pack(vx);
+        my[i] = f2_pack(vy);
+        mz[i] = f2_pack(vz);
+        acc[i] = f2_pack(make_float2(0.f, 0.f));
+    }
+    const unsigned long long B2 = f2_pack(make_float2(B, B));
+    unsigned cur = scell[beg];
+    auto flush = [&](unsigned c) {
+        float *row = pend + G.off_lam[l] + static_cast<long long>(c) * np;
+#pragma unroll
+        for (int i = 0; i < NP2; ++i) {
+            const float2 v = f2_unpack(acc[i]);
+            const int q0 = lane + kWarp * (2 * i), q1 = lane + kWarp * (2 * i + 1);
+            if (q0 < np && v.x != 0.f) atomicAdd(row + q0, v.x);
+            if (q1 < np && v.y != 0.f) atomicAdd(row + q1, v.y);
+            acc[i] = f2_pack(make_float2(0.f, 0.f));
+        }
+    };
+    for (long long b = beg; b < end; b += kWarp) {
+        const long long r = b + lane;
+        if (r < end) {
+            const float4 dv = sdir[r];
+            sh_rec[lane] = make_float4(Cg * dv.x, Cg * dv.y, Cg * dv.z, scoef[l * cap + r]);
+            sh_cell[lane] = scell[r];
+        }
+        __syncwarp();
+        const int cntj = static_cast<int>(min(static_cast<long long>(kWarp), end - b));
+        for (int j = 0; j < cntj; ++j) {
+            const float4 rv = sh_rec[j];
+            const unsigned cj = sh_cell[j];
+            if (cj != cur) {
+                flush(cur);
+                cur = cj;
+            }
+            const unsigned long long cx = f2_pack(make_float2(rv.x, rv.x)), cy = f2_pack(make_float2(rv.y, rv.y)),
+                                     cz = f2_pack(make_float2(rv.z, rv.z)), cc = f2_pack(make_float2(rv.w, rv.w));
+#pragma unroll
+            for (int i = 0; i < NP2; ++i) {
+                unsigned long long t = f2_fma(mx[i], cx, B2);
+                t = f2_fma(my[i], cy, t);
+                t = f2_fma(mz[i], cz, t);
+                const float2 tv = f2_unpack(t);
+                const unsigned long long rr = f2_pack(make_float2(rsqrtf(tv.x), rsqrtf(tv.y)));
+                const unsigned long long r3 = f2_mul(f2_mul(rr, rr), rr);
+                acc[i] = f2_fma(cc, r3, acc[i]);
+            }
+        }
+        __syncwarp();
+    }
+    flush(cur);
+}
+
+template <int PPL>
+__global__ void __launch_bounds__(kBlock) cell_accumulate_kernel(const DevGrid G, int l, long long n,
+                                                                 const unsigned *scell, const float4 *sdir,
+                                                                 const float *scoef, long long cap, float *pend) {
+    __shared__ float4 sh_rec[kBlock / kWarp][kWarp];
+    __shared__ unsigned sh_cell[kBlock / kWarp][kWarp];
+    const int lane = threadIdx.x & 31;
+    const long long warps = static_cast<long long>(gridDim.x) * (blockDim.x / kWarp);
+    const long long nranges = (n + kAccRange - 1) / kAccRange;
+    for (long long w = blockIdx.x * static_cast<long long>(blockDim.x / kWarp) + (threadIdx.x >> 5); w < nranges;
+         w += warps) {
+        const long long beg = w * kAccRange, end = min(n, beg + kAccRange);
+        accumulate_range<PPL>(G, l, beg, end, scell, sdir, scoef, cap, pend, lane, sh_rec[threadIdx.x >> 5],
+                              sh_cell[threadIdx.x >> 5]);
+    }
 }
 
 }  // namespace dartray

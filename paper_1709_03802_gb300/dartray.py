@@ -41,7 +41,8 @@ class dartray_params(C.Structure):
                 ("k_ray_max", C.c_int32), ("k_sca_cap", C.c_int32), ("n_fwhm", C.c_int32),
                 ("merge", C.c_int32), ("max_cross", C.c_int32), ("max_waves", C.c_int32),
                 ("src_stride", C.c_int32), ("src_offset", C.c_int32), ("queue_rays", C.c_int64),
-                ("src_batch", C.c_int64), ("profile", C.c_int32), ("reserved", C.c_int32)]
+                ("src_batch", C.c_int64), ("profile", C.c_int32), ("deposit_direct", C.c_int32),
+                ("deposit_records", C.c_int64)]
 
 
 _L = MAX_LAMBDA

@@ -40,28 +40,32 @@ def check_rfed(gpu, ref, tag=""):
     return rel.max()
 
 
-def check_ledger(st, ref, tag=""):
+def check_ledger(st, ref, tag="", count_rel=1e-4):
     led, cnt = ref.stats()
     for k in ("emitted", "absorbed", "scattered", "escaped", "blocked", "cut"):
         a, b = np.asarray(st[k]), led[k]
         tot = led["emitted"].sum()
         assert np.all(np.abs(a - b) <= REL_TOTAL * max(tot, 1e-300)), f"{tag} ledger {k}: {a} vs {b}"
-    for k in ("crossings", "rays", "splits", "blocks", "escapes", "cuts", "lows", "merges"):
-        assert close_counts(st[k], cnt[k]), f"{tag} count {k}: {st[k]} vs {cnt[k]}"
+    bad = {k: (st[k], cnt[k]) for k in ("crossings", "rays", "splits", "blocks", "escapes", "cuts", "lows", "merges")
+           if not close_counts(st[k], cnt[k], rel=count_rel)}
+    assert not bad, f"{tag} counts (gpu, oracle): {bad}"
 
 
-def run_pair(grid, n_iter, **params):
+ORACLE_KEYS = set(oracle.OracleParams.__dataclass_fields__)
+
+
+def run_pair(grid, n_iter, count_rel=1e-4, **params):
     gpu = DartRay(grid, **params)
-    ref = oracle.Oracle(grid, oracle.OracleParams(**params))
+    ref = oracle.Oracle(grid, oracle.OracleParams(**{k: v for k, v in params.items() if k in ORACLE_KEYS}))
     st = gpu.direct()
     ref.direct()
-    check_ledger(st, ref, "direct")
+    check_ledger(st, ref, "direct", count_rel)
     check_rfed(gpu, ref, "direct")
     assert abs(st["f_u"] - ref.f_u) <= 1e-12 * max(ref.f_u, 1e-300)
     for it in range(n_iter):
         rem, st = gpu.scatter_iter()
         rem_ref = ref.scatter_iter()
-        check_ledger(st, ref, f"iter{it}")
+        check_ledger(st, ref, f"iter{it}", count_rel)
         check_rfed(gpu, ref, f"iter{it}")
         assert abs(rem - rem_ref) <= REL_TOTAL * max(rem_ref, 1e-12)
     return gpu, ref
@@ -113,7 +117,12 @@ def test_point_sources():
                       leaf_of_node=g.leaf_of_node, leaf_lo=g.leaf_lo, leaf_size=g.leaf_size,
                       kappa_rho=g.kappa_rho, emissivity=g.emissivity, albedo=g.albedo, g=g.g,
                       point_xyz=pts, point_lum=np.array([[0.5], [0.25]], np.float32))
-    run_pair(grid, 1, a_rt=0.02, r_pre=0.6)
+    # Point sources sit at non-dyadic positions: ray-face distances are no
+    # longer exact in float32, so a few rays that graze an edge visit a
+    # zero-length cell in one precision and not in the other (each such
+    # crossing deposits nothing) and a few R_pre cuts flip; counts are
+    # compared to 5e-3 here.
+    run_pair(grid, 1, count_rel=5e-3, a_rt=0.02, r_pre=0.6)
 
 
 def test_no_sources_gives_zero():
@@ -210,3 +219,23 @@ def test_map_parity(use_jsca):
     big = b > 1e-6 * b.max()
     assert np.abs(a[big] / b[big] - 1).max() <= REL_CELL
     assert abs(a.sum() / b.sum() - 1) <= REL_TOTAL
+
+
+@pytest.mark.parametrize("records", [0, 5000])
+def test_deferred_deposit_matches_direct_atomics(records):
+    """The deferred per-cell accumulation of crossing records (and its
+    mix with direct atomics when the record buffer is small) gives the same
+    scattering source function as per-pixel atomic deposits."""
+    grid = synth.config1()
+    a = DartRay(grid, r_pre=0.3, deposit_direct=1)
+    b = DartRay(grid, r_pre=0.3, deposit_records=records)
+    for g in (a, b):
+        g.direct()
+        g.scatter_iter()
+    ja, jb = a.jsca("total"), b.jsca("total")
+    big = ja > 1e-6 * ja.max()
+    assert np.abs(jb[big] / ja[big] - 1).max() <= 1e-5
+    Ua, Ub = a.rfed()[0], b.rfed()[0]
+    # U is summed with float atomics in a run-dependent order; a blocking test
+    # that sits on its threshold can flip: 1e-4
+    assert np.abs(Ub / np.maximum(Ua, 1e-30) - 1)[Ua > 1e-6 * Ua.max()].max() <= 1e-4
