@@ -13,7 +13,8 @@ time).  Also reported: seconds per scattering iteration.  The L2 cache is
 flushed (a 512 MB write) between timed steps.
 
 --impl reference times the FP64 CPU oracle (the reference of this build) on
-the host cores on a bounded sample of the same workload (every 400th source).
+the host cores on a bounded sample of the same workload (every 30000th source,
+steps 1-2 and one scattering iteration per step).
 With N > 1 GPUs each rank runs an independent replica (the path has no
 exchange step on one GPU); the value is the sum over ranks.
 """
@@ -110,6 +111,7 @@ class Clocks:
 
 
 def run_step(gpu, grid):
+    """One pass of the hot path: steps 1-2, scattering iterations to f_L, map."""
     st = gpu.direct()
     cross = st["crossings"]
     march_ms = st["march_ms"]
@@ -132,7 +134,7 @@ def run_step(gpu, grid):
     m = gpu.map(OBSERVER, MAP_K, max_sub=MAP_SUB, use_jsca=True)
     launches += 1
     return dict(crossings=cross, march_ms=march_ms, march_crossings=march_cross, jsca_pixels=jpix,
-                iters=it, iter_ms=it_ms, launches=launches, map_sum=float(m.sum()))
+                iters=it, iter_ms=it_ms, launches=launches, map=m)
 
 
 def cpu_sample(grid, params, stride):
@@ -152,10 +154,12 @@ def cpu_sample(grid, params, stride):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-stride", type=int, default=400)
+    ap.add_argument("--cpu-stride", type=int, default=30000)
+    ap.add_argument("--src-stride", type=int, default=1,
+                    help="profiling aid: trace every n-th primary source only (default: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -163,10 +167,15 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     grid, params = make_workload()
+    if args.src_stride > 1:
+        params = dict(params, src_stride=args.src_stride, src_offset=1)
     metric = "ray-cell crossings/s"
     unit = "crossings/s"
     config = {"workload": WORKLOAD, "n_leaf": grid.n_leaf, "a_rt": params["a_rt"], "f_l": F_L,
-              "map": f"nside 64 at {OBSERVER} kpc", "l2": "flushed between steps (512 MB write)"}
+              "map": f"nside 64 at {OBSERVER} kpc", "l2": "flushed between steps (512 MB write)",
+              "warmup_note": "the first warm-up step is the end-to-end run through host buffers"}
+    if args.src_stride > 1:
+        config["profiling_subset"] = f"every {args.src_stride}th primary source (not a bench value)"
 
     if args.impl == "reference":
         if rank != 0:
@@ -181,7 +190,8 @@ def main():
                 tot_c += c
                 tot_t += dt
         v = tot_c / tot_t
-        sample = f"every {args.cpu_stride}th source, steps 1-2 + one scattering iteration"
+        sample = (f"every {args.cpu_stride}th source (and every {args.cpu_stride}th scattering source), "
+                  f"steps 1-2 + one scattering iteration, per step")
         print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": unit, "n_gpus": 0,
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
                           "higher_is_better": True, "dtype": "f64", "data": "synthetic", "config": config,
@@ -203,9 +213,28 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    # warm-up 1: end to end through the C ABI with host buffers -- create (H2D
+    # of the inputs), the whole step, U / L_abs / map back to host
+    e2e = None
+    h2d = sum(np.asarray(a).nbytes for a in (grid.first_child, grid.leaf_of_node, grid.kappa_rho,
+                                             grid.emissivity, grid.albedo, grid.g))
+    if args.warmup >= 1:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g2 = DartRay(grid, **params)
+        r2 = run_step(g2, grid)
+        U, L = g2.rfed()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        d2h = U.nbytes + L.nbytes + r2["map"].nbytes
+        e2e = {"value": r2["crossings"] * world / dt, "unit": unit, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "seconds": dt}
+        g2.close()
+        del g2
+
     gpu = DartRay(grid, profile=1, **params)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
+    for _ in range(max(0, args.warmup - 1)):
         run_step(gpu, grid)
     torch.cuda.synchronize()
     results = []
@@ -237,33 +266,21 @@ def main():
     it_ms = [x for r in results for x in r["iter_ms"]]
     march_ms = sum(r["march_ms"] for r in results)
     nl = grid.n_lambda
-    alg_bytes = sum(r["march_crossings"] * bytes_per_crossing(nl) + 8 * r["jsca_pixels"] for r in results)
+    # algorithmic bytes of the marcher: per crossing (leaf box, face link, node
+    # word, kappa*rho, U_LL, U read-modify-write) plus one 24-byte deposit
+    # record per depositing crossing (j_sca pixels / pixels per row)
+    npx = 12 * 4 ** gpu.k_lam[0]
+    alg_bytes = sum(r["march_crossings"] * bytes_per_crossing(nl) + 24 * r["jsca_pixels"] / npx for r in results)
     peak, peak_src = peaks()
     achieved = alg_bytes / (march_ms / 1e3) / 1e9 if march_ms > 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "kernel": "march_kernel<1,SCATTER/DIRECT/LL>", "peak_source": peak_src,
-                "march_share_of_step": march_ms / total_ms if total_ms else None}
-
-    # end-to-end through the C ABI with host buffers: create (H2D of the
-    # inputs), sweep, U / L_abs / map back to host
-    e2e = None
-    if rank == 0:
-        t0 = time.perf_counter()
-        g2 = DartRay(grid, **params)
-        r2 = run_step(g2, grid)
-        U, L = g2.rfed()
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        h2d = sum(np.asarray(a).nbytes for a in (grid.first_child, grid.leaf_of_node, grid.kappa_rho,
-                                                 grid.emissivity, grid.albedo, grid.g))
-        d2h = U.nbytes + L.nbytes + 4 * nl * 12 * 4 ** MAP_K
-        e2e = {"value": r2["crossings"] / dt, "unit": unit, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "seconds": dt}
-        g2.close()
+                "kernel": "march_kernel (ray marcher)", "peak_source": peak_src,
+                "kernel_busy_share_of_step": march_ms / total_ms if total_ms else None}
+    gpu.close()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.src_stride == 1:
         c, dt = cpu_sample(grid, params, args.cpu_stride)
         cpu = {"value": c / dt, "unit": unit, "cores": 1, "kind": "oracle",
                "sample": f"every {args.cpu_stride}th source, steps 1-2 + one scattering iteration, "

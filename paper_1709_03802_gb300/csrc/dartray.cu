@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <memory>
+#include <utility>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -60,6 +62,29 @@ int k_hp_host(double g, int n_fwhm, int cap) {
 
 }  // namespace
 
+constexpr int kPipes = 2;
+
+struct Pipe {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    PipeDev *d_pd = nullptr;   // device state
+    PipeDev *h_pd = nullptr;   // pinned host copy
+    RayRec *d_H[2] = {nullptr, nullptr}, *d_M[2] = {nullptr, nullptr}, *d_L = nullptr;
+    float *d_HI[2] = {nullptr, nullptr}, *d_MI[2] = {nullptr, nullptr}, *d_LI = nullptr;
+    unsigned long long *d_hkey = nullptr;
+    int *d_hcnt = nullptr;
+    int4 *d_hmem = nullptr;
+    // deferred deposit records
+    unsigned *d_rec_cell = nullptr, *d_srt_cell = nullptr, *d_cnt = nullptr, *d_off = nullptr, *d_cur = nullptr;
+    float4 *d_rec_dir = nullptr, *d_srt_dir = nullptr;
+    float *d_rec_coef = nullptr, *d_srt_coef = nullptr;
+    unsigned long long *d_rec_n = nullptr;
+    int *d_blocksum = nullptr, *d_total = nullptr;
+    // host-side batch bookkeeping
+    bool active = false;
+    int src_lo = 0, nb = 0;
+};
+
 struct dartray_grid {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -82,15 +107,11 @@ struct dartray_grid {
     int *d_src_leaf = nullptr, *d_src_hint = nullptr;
     float4 *d_src_pos = nullptr;
     float *d_src_S = nullptr;
-    // queues
-    RayRec *d_H[2] = {nullptr, nullptr}, *d_M[2] = {nullptr, nullptr}, *d_L = nullptr;
-    float *d_HI[2] = {nullptr, nullptr}, *d_MI[2] = {nullptr, nullptr}, *d_LI = nullptr;
+    // batch pipelines (each with its own stream, queues, merge table and
+    // deposit-record buffer)
+    Pipe pipe[kPipes];
     long long cap = 0;
-    unsigned long long *d_hkey = nullptr;
-    int *d_hcnt = nullptr;
-    int4 *d_hmem = nullptr;
     long long hcap = 0;
-    WaveCounters *d_wc = nullptr;
     DevStats *d_st = nullptr;
     double *d_sum = nullptr;
     double l_sca2 = 0.0;
@@ -99,11 +120,6 @@ struct dartray_grid {
     int num_sms = 1;
     int march_blocks = 1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // deferred deposit records
-    unsigned *d_rec_cell = nullptr, *d_srt_cell = nullptr, *d_cnt = nullptr, *d_off = nullptr, *d_cur = nullptr;
-    float4 *d_rec_dir = nullptr, *d_srt_dir = nullptr;
-    float *d_rec_coef = nullptr, *d_srt_coef = nullptr;
-    unsigned long long *d_rec_n = nullptr;
     long long rec_cap = 0;
     cudaEvent_t mev0 = nullptr, mev1 = nullptr;  // around each march launch (profile mode)
     double march_ms = 0.0;
@@ -113,15 +129,24 @@ struct dartray_grid {
 namespace {
 
 void free_all(dartray_grid *g) {
-    void *ptrs[] = {g->d_ztab, g->d_node_child, g->d_rope, g->d_node_box, g->d_leaf_box, g->d_dirtab, g->d_kr, g->d_emis,
-                    g->d_pxyz, g->d_plum, g->d_U, g->d_ULL, g->d_pend[0], g->d_pend[1], g->d_jtot, g->d_flags,
-                    g->d_blocksum, g->d_total, g->d_src_idx, g->d_src_leaf, g->d_src_hint, g->d_src_pos,
-                    g->d_src_S, g->d_H[0], g->d_H[1], g->d_M[0], g->d_M[1], g->d_L, g->d_HI[0], g->d_HI[1],
-                    g->d_MI[0], g->d_MI[1], g->d_LI, g->d_hkey, g->d_hcnt, g->d_hmem, g->d_wc, g->d_st, g->d_sum,
-                    g->d_rec_cell, g->d_srt_cell, g->d_cnt, g->d_off, g->d_cur, g->d_rec_dir, g->d_srt_dir, g->d_rec_coef,
-                    g->d_srt_coef, g->d_rec_n};
+    void *ptrs[] = {g->d_ztab, g->d_node_child, g->d_rope, g->d_node_box, g->d_leaf_box, g->d_dirtab, g->d_kr,
+                    g->d_emis, g->d_pxyz, g->d_plum, g->d_U, g->d_ULL, g->d_pend[0], g->d_pend[1], g->d_jtot,
+                    g->d_flags, g->d_blocksum, g->d_total, g->d_src_idx, g->d_src_leaf, g->d_src_hint,
+                    g->d_src_pos, g->d_src_S, g->d_st, g->d_sum};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (int i = 0; i < kPipes; ++i) {
+        Pipe &P = g->pipe[i];
+        void *pp[] = {P.d_pd, P.d_H[0], P.d_H[1], P.d_M[0], P.d_M[1], P.d_L, P.d_HI[0], P.d_HI[1], P.d_MI[0],
+                      P.d_MI[1], P.d_LI, P.d_hkey, P.d_hcnt, P.d_hmem, P.d_rec_cell, P.d_srt_cell, P.d_cnt,
+                      P.d_off, P.d_cur, P.d_rec_dir, P.d_srt_dir, P.d_rec_coef, P.d_srt_coef, P.d_rec_n,
+                      P.d_blocksum, P.d_total};
+        for (void *p : pp)
+            if (p) cudaFree(p);
+        if (P.h_pd) cudaFreeHost(P.h_pd);
+        if (P.ev) cudaEventDestroy(P.ev);
+        if (P.stream) cudaStreamDestroy(P.stream);
+    }
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     if (g->mev0) cudaEventDestroy(g->mev0);
@@ -156,23 +181,23 @@ int occupancy_blocks(const void *kernel, int num_sms) {
 }
 
 template <int NL>
-int launch_march_nl(dartray_grid *g, int mode, const MarchArgs &A) {
+int launch_march_nl(dartray_grid *g, cudaStream_t st, int mode, const MarchArgs &A) {
     const int blocks = g->march_blocks;
-    if (mode == MODE_LL) march_kernel<NL, MODE_LL><<<blocks, kBlock, 0, g->stream>>>(g->G, A);
-    else if (mode == MODE_DIRECT) march_kernel<NL, MODE_DIRECT><<<blocks, kBlock, 0, g->stream>>>(g->G, A);
-    else march_kernel<NL, MODE_SCATTER><<<blocks, kBlock, 0, g->stream>>>(g->G, A);
+    if (mode == MODE_LL) march_kernel<NL, MODE_LL><<<blocks, kBlock, 0, st>>>(g->G, A);
+    else if (mode == MODE_DIRECT) march_kernel<NL, MODE_DIRECT><<<blocks, kBlock, 0, st>>>(g->G, A);
+    else march_kernel<NL, MODE_SCATTER><<<blocks, kBlock, 0, st>>>(g->G, A);
     ++g->launches;
     CK(cudaGetLastError());
     return DARTRAY_OK;
 }
 
-int launch_march(dartray_grid *g, int mode, const MarchArgs &A) {
+int launch_march(dartray_grid *g, cudaStream_t st, int mode, const MarchArgs &A) {
     switch (g->nl) {
-    case 1: return launch_march_nl<1>(g, mode, A);
-    case 2: return launch_march_nl<2>(g, mode, A);
-    case 4: return launch_march_nl<4>(g, mode, A);
-    case 8: return launch_march_nl<8>(g, mode, A);
-    case 16: return launch_march_nl<16>(g, mode, A);
+    case 1: return launch_march_nl<1>(g, st, mode, A);
+    case 2: return launch_march_nl<2>(g, st, mode, A);
+    case 4: return launch_march_nl<4>(g, st, mode, A);
+    case 8: return launch_march_nl<8>(g, st, mode, A);
+    case 16: return launch_march_nl<16>(g, st, mode, A);
     default: return fail(DARTRAY_E_INVAL, "n_lambda must be 1, 2, 4, 8 or 16");
     }
 }
@@ -183,8 +208,8 @@ int build_sources(dartray_grid *g, int mode, const float *pend_src, int *n_src) 
     const int nb = (n_all + kBlock - 1) / kBlock;
     source_flags_kernel<<<nb, kBlock, 0, g->stream>>>(g->G, mode, pend_src, g->P.src_stride, g->P.src_offset,
                                                       g->d_flags);
-    scan_blocks_kernel<<<nb, kBlock, 0, g->stream>>>(g->d_flags, n_all, g->d_blocksum);
-    scan_offsets_kernel<<<1, 1, 0, g->stream>>>(g->d_blocksum, nb, g->d_total);
+    scan_blocks_kernel<<<nb, kBlock, 0, g->stream>>>(nullptr, g->d_flags, n_all, g->d_blocksum);
+    scan_offsets_kernel<<<1, 1, 0, g->stream>>>(nullptr, g->d_blocksum, nb, g->d_total);
     scatter_compact_kernel<<<nb, kBlock, 0, g->stream>>>(g->d_flags, n_all, g->d_blocksum, g->d_src_idx);
     g->launches += 4;
     CK(cudaGetLastError());
@@ -201,137 +226,168 @@ int build_sources(dartray_grid *g, int mode, const float *pend_src, int *n_src) 
     return DARTRAY_OK;
 }
 
-// Expand the buffered crossing records into the pending j_sca rows: bucket
-// the records by cell and let one warp accumulate each cell's row.
-int flush_records(dartray_grid *g, float *pend_dst) {
+// Enqueue on pipeline P's stream the expansion of its buffered crossing
+// records into the pending j_sca rows (bucket by cell, then per-cell-range
+// accumulation).  On the device the kernels run only when the buffer is at
+// least half full, or always when force is set.
+int enqueue_flush(dartray_grid *g, Pipe &P, float *pend_dst, int force) {
     if (g->rec_cap == 0) return DARTRAY_OK;
-    unsigned long long n = 0;
-    CK(cudaMemcpyAsync(&n, g->d_rec_n, sizeof n, cudaMemcpyDeviceToHost, g->stream));
-    CK(cudaStreamSynchronize(g->stream));
-    if (n == 0) return DARTRAY_OK;
-    const long long nr = std::min<long long>(static_cast<long long>(n), g->rec_cap);
-    cudaStream_t s = g->stream;
+    cudaStream_t s = P.stream;
     const int nb = (g->n_leaf + kBlock - 1) / kBlock;
-    const int gb = std::max(1, std::min<int>(static_cast<int>((nr + kBlock - 1) / kBlock), 8 * g->num_sms));
-    // per-cell counts were taken by the marcher
-    scan_blocks_kernel<<<nb, kBlock, 0, s>>>(reinterpret_cast<const int *>(g->d_cnt), g->n_leaf, g->d_blocksum);
-    scan_offsets_kernel<<<1, 1, 0, s>>>(g->d_blocksum, nb, g->d_total);
-    scan_apply_kernel<<<nb, kBlock, 0, s>>>(g->d_cnt, g->n_leaf, g->d_blocksum, g->d_off, g->d_cur);
-    rec_scatter_kernel<<<gb, kBlock, 0, s>>>(g->d_rec_cell, g->d_rec_dir, g->d_rec_coef, nr, g->rec_cap, g->nl,
-                                             g->d_cur, g->d_srt_cell, g->d_srt_dir, g->d_srt_coef);
+    const unsigned gb = static_cast<unsigned>(8 * g->num_sms);
+    flush_decide_kernel<<<1, 1, 0, s>>>(P.d_pd, P.d_rec_n, g->rec_cap, force);
+    scan_blocks_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, reinterpret_cast<const int *>(P.d_cnt), g->n_leaf, P.d_blocksum);
+    scan_offsets_kernel<<<1, 1, 0, s>>>(P.d_pd, P.d_blocksum, nb, P.d_total);
+    scan_apply_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, P.d_cnt, g->n_leaf, P.d_blocksum, P.d_off, P.d_cur);
+    rec_scatter_kernel<<<gb, kBlock, 0, s>>>(P.d_pd, P.d_rec_n, P.d_rec_cell, P.d_rec_dir, P.d_rec_coef, g->rec_cap,
+                                             g->nl, P.d_cur, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef);
     for (int l = 0; l < g->nl; ++l) {
-        const unsigned gbl = static_cast<unsigned>(8 * g->num_sms);
         switch (g->k_lam[l]) {
-        case 0: cell_accumulate_kernel<1><<<gbl, kBlock, 0, s>>>(g->G, l, nr, g->d_srt_cell, g->d_srt_dir, g->d_srt_coef, g->rec_cap, pend_dst); break;
-        case 1: cell_accumulate_kernel<2><<<gbl, kBlock, 0, s>>>(g->G, l, nr, g->d_srt_cell, g->d_srt_dir, g->d_srt_coef, g->rec_cap, pend_dst); break;
-        case 2: cell_accumulate_kernel<6><<<gbl, kBlock, 0, s>>>(g->G, l, nr, g->d_srt_cell, g->d_srt_dir, g->d_srt_coef, g->rec_cap, pend_dst); break;
-        default: cell_accumulate_kernel<24><<<gbl, kBlock, 0, s>>>(g->G, l, nr, g->d_srt_cell, g->d_srt_dir, g->d_srt_coef, g->rec_cap, pend_dst); break;
+        case 0: cell_accumulate_kernel<1><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_rec_n, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
+        case 1: cell_accumulate_kernel<2><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_rec_n, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
+        case 2: cell_accumulate_kernel<6><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_rec_n, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
+        default: cell_accumulate_kernel<24><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_rec_n, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
         }
     }
-    g->launches += 4 + g->nl;
+    flush_reset_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, P.d_rec_n, P.d_cnt, g->n_leaf);
+    g->launches += 6 + g->nl;
     CK(cudaGetLastError());
-    CK(cudaMemsetAsync(g->d_rec_n, 0, sizeof(unsigned long long), s));
-    CK(cudaMemsetAsync(g->d_cnt, 0, static_cast<size_t>(g->n_leaf) * sizeof(unsigned), s));
     return DARTRAY_OK;
 }
 
-// Waves of one batch of sources [src_lo, src_lo + nb_src).
-int run_batch(dartray_grid *g, int mode, MarchArgs base, int src_lo, int nb_src, int kstart, int *status,
-              long long *waves, long long *peak) {
-    long long nA = static_cast<long long>(nb_src) * (12ll << (2 * kstart));
-    long long nB = 0;
-    int wave_kind = 0, par = 0;
-    WaveCounters wc{};
-    for (int w = 0;; ++w) {
-        if (nA + nB == 0) break;
-        if (w >= g->P.max_waves) return fail(DARTRAY_E_LIMIT, "wave cap reached");
-        *peak = std::max(*peak, nA + nB);
-        CK(cudaMemsetAsync(g->d_wc, 0, sizeof(WaveCounters), g->stream));
-        MarchArgs A = base;
-        A.wave_kind = wave_kind;
-        A.nA = nA;
-        A.nB = nB;
-        A.H_in = g->d_H[par];
-        A.H_in_I = g->d_HI[par];
-        A.M_in = g->d_M[par];
-        A.M_in_I = g->d_MI[par];
-        A.kstart = kstart;
-        A.src_lo = src_lo;
-        A.H_out = g->d_H[1 - par];
-        A.H_out_I = g->d_HI[1 - par];
-        A.L_out = g->d_L;
-        A.L_out_I = g->d_LI;
-        if (g->P.profile) CK(cudaEventRecord(g->mev0, g->stream));
-        int rc = launch_march(g, mode, A);
-        if (rc) return rc;
-        if (g->P.profile) CK(cudaEventRecord(g->mev1, g->stream));
-        ++g->march_launches;
-        CK(cudaMemcpyAsync(&wc, g->d_wc, sizeof(WaveCounters), cudaMemcpyDeviceToHost, g->stream));
-        CK(cudaStreamSynchronize(g->stream));
-        if (g->P.profile) {
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, g->mev0, g->mev1));
-            g->march_ms += ms;
+struct MarchTiming {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[kPipes];
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<float, float>> spans;  // [start, end] ms after the phase origin
+    cudaEvent_t origin = nullptr;
+
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
         }
-        if (wc.status & ST_QUEUE) { *status = ST_QUEUE; return DARTRAY_OK; }
-        if (mode != MODE_LL && g->rec_cap > 0) {
-            unsigned long long nrec = 0;
-            CK(cudaMemcpyAsync(&nrec, g->d_rec_n, sizeof nrec, cudaMemcpyDeviceToHost, g->stream));
-            CK(cudaStreamSynchronize(g->stream));
-            if (static_cast<long long>(nrec) >= g->rec_cap / 2) {
-                int rcf = flush_records(g, base.pend_dst);
-                if (rcf) return rcf;
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    // collect the spans of pipeline i (its stream is synchronised)
+    void collect(int i) {
+        for (auto &pr : pending[i]) {
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, origin, pr.first);
+            cudaEventElapsedTime(&b, origin, pr.second);
+            spans.emplace_back(a, b);
+            pool.push_back(pr.first);
+            pool.push_back(pr.second);
+        }
+        pending[i].clear();
+    }
+    // length of the union of all spans
+    double busy_ms() {
+        std::sort(spans.begin(), spans.end());
+        double tot = 0.0, cs = -1e30, ce = -1e30;
+        for (auto &sp : spans) {
+            if (sp.first > ce) {
+                if (ce > cs) tot += ce - cs;
+                cs = sp.first;
+                ce = sp.second;
+            } else {
+                ce = std::max<double>(ce, sp.second);
             }
         }
-        if (wc.status & ST_CROSS_CAP) {
-            char m[256];
-            std::snprintf(m, sizeof m,
-                          "crossing cap per ray reached (mode %d, source %d, level %d, pixel %llu, kind %d, "
-                          "leaf %d, d %.9g, side %.9g)",
-                          mode, wc.dbg_src, wc.dbg_lev, static_cast<unsigned long long>(wc.dbg_pix), wc.dbg_kind,
-                          wc.dbg_leaf, static_cast<double>(wc.dbg_d), static_cast<double>(wc.dbg_te));
-            return fail(DARTRAY_E_LIMIT, m);
-        }
-        if (wc.status & ST_NOPROGRESS) return fail(DARTRAY_E_LIMIT, "ray made no progress across a face");
-        DevStats *st = g->d_st;
-        unsigned long long n_next = 0;
-        if (wc.n_low > 0) {
-            long long hc = 1;
-            while (hc < 2 * static_cast<long long>(wc.n_low)) hc <<= 1;
-            if (hc > g->hcap) return fail(DARTRAY_E_QUEUE, "merge table too small");
-            CK(cudaMemsetAsync(g->d_hkey, 0xff, hc * sizeof(unsigned long long), g->stream));
-            CK(cudaMemsetAsync(g->d_hcnt, 0, hc * sizeof(int), g->stream));
-            MergeArgs M{};
-            M.L = g->d_L;
-            M.L_I = g->d_LI;
-            M.n_low = static_cast<long long>(wc.n_low);
-            M.cap = g->cap;
-            M.hkey = g->d_hkey;
-            M.hcnt = g->d_hcnt;
-            M.hmem = g->d_hmem;
-            M.hcap = hc;
-            M.M_out = g->d_M[1 - par];
-            M.M_out_I = g->d_MI[1 - par];
-            M.wc = g->d_wc;
-            M.st = st;
-            M.nl = g->nl;
-            merge_insert_kernel<<<static_cast<unsigned>((M.n_low + kBlock - 1) / kBlock), kBlock, 0, g->stream>>>(M);
-            merge_emit_kernel<<<static_cast<unsigned>((hc + kBlock - 1) / kBlock), kBlock, 0, g->stream>>>(M);
-            g->launches += 2;
-            CK(cudaGetLastError());
-            CK(cudaMemcpyAsync(&wc, g->d_wc, sizeof(WaveCounters), cudaMemcpyDeviceToHost, g->stream));
-            CK(cudaStreamSynchronize(g->stream));
-            if (wc.status & ST_QUEUE) { *status = ST_QUEUE; return DARTRAY_OK; }
-            if (wc.status & ST_MERGE) return fail(DARTRAY_E_QUEUE, "merge table overflow");
-            n_next = wc.n_next;
-        }
-        *status = 0;
-        ++*waves;
-        nA = 4 * static_cast<long long>(wc.n_high);
-        nB = static_cast<long long>(n_next);
-        wave_kind = 1;
-        par = 1 - par;
+        if (ce > cs) tot += ce - cs;
+        return tot;
     }
+    ~MarchTiming() {
+        for (auto &v : pending)
+            for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+// Enqueue one wave of pipeline P: march, merge the low list, flush records
+// when the buffer is half full, advance to the next wave.
+int enqueue_wave(dartray_grid *g, Pipe &P, int pi, int mode, const MarchArgs &base, float *pend_dst,
+                 MarchTiming *tm) {
+    cudaStream_t s = P.stream;
+    MarchArgs A = base;
+    A.pd = P.d_pd;
+    for (int i = 0; i < 2; ++i) {
+        A.Hb[i] = P.d_H[i];
+        A.HIb[i] = P.d_HI[i];
+        A.Mb[i] = P.d_M[i];
+        A.MIb[i] = P.d_MI[i];
+    }
+    A.L_out = P.d_L;
+    A.L_out_I = P.d_LI;
+    A.rec_cell = P.d_rec_cell;
+    A.rec_dir = P.d_rec_dir;
+    A.rec_coef = P.d_rec_coef;
+    A.rec_n = P.d_rec_n;
+    A.rec_cnt = P.d_cnt;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (tm) {
+        e0 = tm->get();
+        e1 = tm->get();
+        CK(cudaEventRecord(e0, s));
+    }
+    int rc = launch_march(g, s, mode, A);
+    if (rc) return rc;
+    if (tm) {
+        CK(cudaEventRecord(e1, s));
+        tm->pending[pi].emplace_back(e0, e1);
+    }
+    ++g->march_launches;
+    MergeArgs M{};
+    M.pd = P.d_pd;
+    M.L = P.d_L;
+    M.L_I = P.d_LI;
+    M.cap = g->cap;
+    M.hkey = P.d_hkey;
+    M.hcnt = P.d_hcnt;
+    M.hmem = P.d_hmem;
+    M.hcap = g->hcap;
+    for (int i = 0; i < 2; ++i) {
+        M.Mb[i] = P.d_M[i];
+        M.MIb[i] = P.d_MI[i];
+    }
+    M.st = g->d_st;
+    M.nl = g->nl;
+    const unsigned mg = static_cast<unsigned>(2 * g->num_sms);
+    merge_size_kernel<<<1, 1, 0, s>>>(P.d_pd, g->hcap);
+    merge_clear_kernel<<<mg, kBlock, 0, s>>>(M);
+    merge_insert_kernel<<<mg, kBlock, 0, s>>>(M);
+    merge_emit_kernel<<<mg, kBlock, 0, s>>>(M);
+    g->launches += 4;
+    if (mode != MODE_LL) {
+        rc = enqueue_flush(g, P, pend_dst, 0);
+        if (rc) return rc;
+    }
+    wave_advance_kernel<<<1, 1, 0, s>>>(P.d_pd);
+    ++g->launches;
+    CK(cudaGetLastError());
+    return DARTRAY_OK;
+}
+
+int start_batch(dartray_grid *g, Pipe &P, int src_lo, int nb, int kstart) {
+    PipeDev &h = *P.h_pd;
+    std::memset(&h, 0, sizeof h);
+    h.nA = static_cast<long long>(nb) * (12ll << (2 * kstart));
+    h.nB = 0;
+    h.kind = 0;
+    h.par = 0;
+    h.src_lo = src_lo;
+    h.nb_src = nb;
+    h.kstart = kstart;
+    h.done = 0;
+    h.peak = h.nA;
+    h.waves = 1;
+    h.max_waves = g->P.max_waves;
+    CK(cudaMemcpyAsync(P.d_pd, P.h_pd, sizeof(PipeDev), cudaMemcpyHostToDevice, P.stream));
+    P.active = true;
+    P.src_lo = src_lo;
+    P.nb = nb;
     return DARTRAY_OK;
 }
 
@@ -341,6 +397,23 @@ struct PhaseResult {
     double f_u;
     double pend_sum;
 };
+
+int status_error(const PipeDev &h, int mode) {
+    const WaveCounters &wc = h.wc;
+    if (wc.status & ST_CROSS_CAP) {
+        char m[256];
+        std::snprintf(m, sizeof m,
+                      "crossing cap per ray reached (mode %d, source %d, level %d, pixel %llu, kind %d, "
+                      "leaf %d, d %.9g, side %.9g)",
+                      mode, wc.dbg_src, wc.dbg_lev, static_cast<unsigned long long>(wc.dbg_pix), wc.dbg_kind,
+                      wc.dbg_leaf, static_cast<double>(wc.dbg_d), static_cast<double>(wc.dbg_te));
+        return fail(DARTRAY_E_LIMIT, m);
+    }
+    if (wc.status & ST_NOPROGRESS) return fail(DARTRAY_E_LIMIT, "ray made no progress across a face");
+    if (wc.status & ST_WAVE_CAP) return fail(DARTRAY_E_LIMIT, "wave cap reached");
+    if (wc.status & ST_MERGE) return fail(DARTRAY_E_QUEUE, "merge table overflow");
+    return DARTRAY_OK;
+}
 
 // One phase (mode: step 1, step 2, one scattering iteration).
 int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
@@ -377,23 +450,19 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
     base.k_ray_max = g->P.k_ray_max;
     base.merge = g->P.merge;
     base.max_cross = g->P.max_cross;
-    base.wc = g->d_wc;
     base.st = g->d_st;
-    base.rec_cell = g->d_rec_cell;
-    base.rec_dir = g->d_rec_dir;
-    base.rec_coef = g->d_rec_coef;
-    base.rec_n = g->d_rec_n;
-    base.rec_cnt = g->d_cnt;
     base.rec_cap = g->rec_cap;
 
     // Sources are traced in batches (the phase is additive over sources and
-    // U_LL is fixed during a phase, so batching does not change the result).
-    // The batch size follows the peak rays per source of a wave seen so far,
-    // so that a wave fits the queues; an overflow restarts the phase with
-    // smaller batches.
+    // U_LL is fixed during a phase, so batching does not change the result),
+    // two batches at a time on two streams so that one batch's last waves
+    // overlap the other's.  The batch size follows the peak rays per source
+    // of a wave seen so far; an overflow restarts the phase with smaller
+    // batches.
     const long long npix0 = 12ll << (2 * kstart);
     long long batch_cap = g->P.src_batch > 0 ? g->P.src_batch : n_src;
-    double rays_per_src = static_cast<double>(npix0) * 16.0;  // first guess: growth 16x
+    double rays_per_src = static_cast<double>(npix0) * 16.0;
+    constexpr int kWavesAhead = 6;
     DevStats snap{};
     CK(cudaMemcpyAsync(&snap, g->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -410,29 +479,77 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
             }
             CK(cudaMemsetAsync(pend_dst, 0, g->sca_len * sizeof(float), s));
         }
-        if (g->rec_cap > 0) {
-            CK(cudaMemsetAsync(g->d_rec_n, 0, sizeof(unsigned long long), s));
-            CK(cudaMemsetAsync(g->d_cnt, 0, static_cast<size_t>(g->n_leaf) * sizeof(unsigned), s));
+        for (int i = 0; i < kPipes; ++i) {
+            Pipe &P = g->pipe[i];
+            P.active = false;
+            if (g->rec_cap > 0) {
+                CK(cudaMemsetAsync(P.d_rec_n, 0, sizeof(unsigned long long), s));
+                CK(cudaMemsetAsync(P.d_cnt, 0, static_cast<size_t>(g->n_leaf) * sizeof(unsigned), s));
+            }
         }
         DevStats fresh = snap;
         std::memset(fresh.ledger, 0, sizeof fresh.ledger);
         CK(cudaMemcpyAsync(g->d_st, &fresh, sizeof(DevStats), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));  // the pipelines start after the setup
+        std::unique_ptr<MarchTiming> tm;
+        if (g->P.profile) {
+            tm.reset(new MarchTiming());
+            CK(cudaEventCreate(&tm->origin));
+            CK(cudaEventRecord(tm->origin, s));
+            CK(cudaEventSynchronize(tm->origin));
+        }
         long long waves = 0;
         bool overflow = false;
         long long failed_nb = 0;
-        for (long long lo = 0; lo < n_src;) {
-            long long want = static_cast<long long>(0.8 * static_cast<double>(g->cap) / rays_per_src);
-            want = std::max<long long>(1, std::min(want, batch_cap));
-            const int nb = static_cast<int>(std::min<long long>(want, n_src - lo));
-            int status = 0;
-            long long peak = 0;
-            rc = run_batch(g, mode, base, static_cast<int>(lo), nb, kstart, &status, &waves, &peak);
-            if (rc) return rc;
-            if (status == ST_QUEUE) { overflow = true; failed_nb = nb; break; }
-            rays_per_src = std::max(rays_per_src * 0.5, static_cast<double>(peak) / nb);
-            lo += nb;
+        long long next = 0;
+        for (;;) {
+            bool any = false;
+            for (int i = 0; i < kPipes; ++i) {
+                Pipe &P = g->pipe[i];
+                if (!P.active && next < n_src) {
+                    long long want = static_cast<long long>(0.8 * static_cast<double>(g->cap) / rays_per_src);
+                    want = std::max<long long>(1, std::min(want, batch_cap));
+                    const int nb = static_cast<int>(std::min<long long>(want, n_src - next));
+                    if ((rc = start_batch(g, P, static_cast<int>(next), nb, kstart))) return rc;
+                    next += nb;
+                }
+                if (P.active) {
+                    any = true;
+                    for (int w = 0; w < kWavesAhead; ++w)
+                        if ((rc = enqueue_wave(g, P, i, mode, base, pend_dst, tm.get()))) return rc;
+                    CK(cudaMemcpyAsync(P.h_pd, P.d_pd, sizeof(PipeDev), cudaMemcpyDeviceToHost, P.stream));
+                    CK(cudaEventRecord(P.ev, P.stream));
+                }
+            }
+            if (!any) break;
+            for (int i = 0; i < kPipes; ++i) {
+                Pipe &P = g->pipe[i];
+                if (!P.active) continue;
+                CK(cudaEventSynchronize(P.ev));
+                if (tm) tm->collect(i);
+                const PipeDev &h = *P.h_pd;
+                if (h.wc.status & ST_QUEUE) {
+                    overflow = true;
+                    failed_nb = std::max<long long>(failed_nb, P.nb);
+                } else if ((rc = status_error(h, mode))) {
+                    return rc;
+                }
+                if (h.done) {
+                    P.active = false;
+                    waves += h.waves;
+                    rays_per_src = std::max(rays_per_src * 0.5, static_cast<double>(h.peak) / P.nb);
+                }
+            }
+            if (overflow) break;
         }
+        for (int i = 0; i < kPipes; ++i) CK(cudaStreamSynchronize(g->pipe[i].stream));
         if (!overflow) {
+            // last records of both pipelines
+            for (int i = 0; i < kPipes && mode != MODE_LL; ++i) {
+                if ((rc = enqueue_flush(g, g->pipe[i], pend_dst, 1))) return rc;
+                CK(cudaStreamSynchronize(g->pipe[i].stream));
+            }
+            if (tm) g->march_ms += tm->busy_ms();
             DevStats out{};
             CK(cudaMemcpyAsync(&out, g->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
@@ -450,8 +567,6 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
     res->f_u = f_u;
     res->pend_sum = 0.0;
     if (mode != MODE_LL) {
-        rc = flush_records(g, pend_dst);
-        if (rc) return rc;
         CK(cudaMemsetAsync(g->d_sum, 0, sizeof(double), s));
         accumulate_pending_kernel<<<4 * g->num_sms, kBlock, 0, s>>>(pend_dst, g->d_jtot, g->sca_len, g->d_sum);
         ++g->launches;
@@ -595,12 +710,14 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
     // automatic sizes: large enough for the biggest waves of galaxy-sized
     // grids, small for small grids
     g->cap = P.queue_rays > 0 ? P.queue_rays
-                              : std::min<long long>(1ll << 26, std::max<long long>(1ll << 20, 256ll * desc->n_leaf));
+                              : std::min<long long>(1ll << 27, std::max<long long>(1ll << 20, 512ll * desc->n_leaf));
     g->rec_cap = P.deposit_direct ? 0
                  : (P.deposit_records > 0 ? P.deposit_records
-                                          : std::min<long long>(1ll << 27, std::max<long long>(1ll << 20, 512ll * desc->n_leaf)));
+                                          : std::min<long long>(1ll << 28, std::max<long long>(1ll << 20, 1024ll * desc->n_leaf)));
+    // merge table: low lists are far smaller than waves; a wave whose low list
+    // does not fit is retried with a smaller source batch
     g->hcap = 1;
-    while (g->hcap < 2 * g->cap) g->hcap <<= 1;
+    while (g->hcap < std::min<long long>(2 * g->cap, 1ll << 27)) g->hcap <<= 1;
     const int n_all = desc->n_leaf + desc->n_point;
     const int nblk = (n_all + kBlock - 1) / kBlock;
 #define AL(ptr, cnt)                                                                              \
@@ -632,31 +749,43 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
     AL(g->d_src_hint, n_all);
     AL(g->d_src_pos, n_all);
     AL(g->d_src_S, static_cast<size_t>(n_all) * nl);
-    for (int i = 0; i < 2; ++i) {
-        AL(g->d_H[i], g->cap);
-        AL(g->d_M[i], g->cap);
-        AL(g->d_HI[i], static_cast<size_t>(g->cap) * nl);
-        AL(g->d_MI[i], static_cast<size_t>(g->cap) * nl);
-    }
-    AL(g->d_L, g->cap);
-    AL(g->d_LI, static_cast<size_t>(g->cap) * nl);
-    AL(g->d_hkey, g->hcap);
-    AL(g->d_hcnt, g->hcap);
-    AL(g->d_hmem, g->hcap);
-    AL(g->d_wc, 1);
     AL(g->d_st, 1);
     AL(g->d_sum, 1);
-    if (g->rec_cap > 0) {
-        AL(g->d_rec_cell, g->rec_cap);
-        AL(g->d_srt_cell, g->rec_cap);
-        AL(g->d_rec_dir, g->rec_cap);
-        AL(g->d_srt_dir, g->rec_cap);
-        AL(g->d_rec_coef, static_cast<size_t>(g->rec_cap) * nl);
-        AL(g->d_srt_coef, static_cast<size_t>(g->rec_cap) * nl);
-        AL(g->d_cnt, desc->n_leaf);
-        AL(g->d_off, desc->n_leaf);
-        AL(g->d_cur, desc->n_leaf);
-        AL(g->d_rec_n, 1);
+    const int nblk_leaf = (desc->n_leaf + kBlock - 1) / kBlock;
+    for (int p = 0; p < kPipes; ++p) {
+        Pipe &P = g->pipe[p];
+        for (int i = 0; i < 2; ++i) {
+            AL(P.d_H[i], g->cap);
+            AL(P.d_M[i], g->cap);
+            AL(P.d_HI[i], static_cast<size_t>(g->cap) * nl);
+            AL(P.d_MI[i], static_cast<size_t>(g->cap) * nl);
+        }
+        AL(P.d_L, g->cap);
+        AL(P.d_LI, static_cast<size_t>(g->cap) * nl);
+        AL(P.d_hkey, g->hcap);
+        AL(P.d_hcnt, g->hcap);
+        AL(P.d_hmem, g->hcap);
+        AL(P.d_pd, 1);
+        if (g->rec_cap > 0) {
+            AL(P.d_rec_cell, g->rec_cap);
+            AL(P.d_srt_cell, g->rec_cap);
+            AL(P.d_rec_dir, g->rec_cap);
+            AL(P.d_srt_dir, g->rec_cap);
+            AL(P.d_rec_coef, static_cast<size_t>(g->rec_cap) * nl);
+            AL(P.d_srt_coef, static_cast<size_t>(g->rec_cap) * nl);
+            AL(P.d_cnt, desc->n_leaf);
+            AL(P.d_off, desc->n_leaf);
+            AL(P.d_cur, desc->n_leaf);
+            AL(P.d_rec_n, 1);
+            AL(P.d_blocksum, nblk_leaf + 1);
+            AL(P.d_total, 1);
+        }
+        if (cudaMallocHost(reinterpret_cast<void **>(&P.h_pd), sizeof(PipeDev)) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&P.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P.ev, cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(DARTRAY_E_CUDA, "pipeline stream setup failed"));
+        if (cudaMemsetAsync(P.d_pd, 0, sizeof(PipeDev), g->stream) != cudaSuccess)
+            return bail(fail(DARTRAY_E_CUDA, "memset failed"));
     }
 #undef AL
     cudaStream_t s = g->stream;

@@ -237,14 +237,35 @@ __device__ inline int locate_root(const DevGrid &G, const float3 p, const float3
 // Next leaf after leaving `leaf` through the faces in `tie` at exit point pe.
 // Uses the face link of the lowest tied axis; falls back to a root descent
 // when pe lies outside the linked node (edge/corner exits).
-__device__ inline int next_leaf(const DevGrid &G, int leaf, int tie, const float3 pe, const float3 n) {
+// Face links: >= 0 a refined node, -1 the model boundary, <= -2 a leaf
+// (-(leaf + 2)).  On return *box holds the new leaf's box when the link led
+// straight to a leaf (has_box = true).
+__device__ inline int next_leaf(const DevGrid &G, int leaf, int tie, const float3 pe, const float3 n, float4 *box,
+                                bool *has_box) {
     const int a = __ffs(tie) - 1;
     const float na = a == 0 ? n.x : (a == 1 ? n.y : n.z);
     const int nb = __ldg(&G.leaf_rope[6 * leaf + 2 * a + (na > 0.f ? 1 : 0)]);
-    if (nb < 0) return -1;
+    *has_box = false;
+    if (nb == -1) return -1;
+    if (nb <= -2) {
+        const int lf = -nb - 2;
+        const float4 b = __ldg(&G.leaf_box[lf]);
+        if (inside_box(b, pe, n)) {
+            *box = b;
+            *has_box = true;
+            return lf;
+        }
+        return locate_root(G, pe, n);
+    }
     const float4 b = __ldg(&G.node_box[nb]);
     if (inside_box(b, pe, n)) return descend(G, nb, b, pe, n);
     return locate_root(G, pe, n);
+}
+
+__device__ inline int next_leaf(const DevGrid &G, int leaf, int tie, const float3 pe, const float3 n) {
+    float4 b;
+    bool hb;
+    return next_leaf(G, leaf, tie, pe, n, &b, &hb);
 }
 
 // ------------------------------------------------------------------ rays
@@ -281,7 +302,7 @@ struct DevStats {
 };
 
 // device status word
-enum { ST_OK = 0, ST_CROSS_CAP = 1, ST_QUEUE = 2, ST_NOPROGRESS = 4, ST_MERGE = 8 };
+enum { ST_OK = 0, ST_CROSS_CAP = 1, ST_QUEUE = 2, ST_NOPROGRESS = 4, ST_MERGE = 8, ST_WAVE_CAP = 16 };
 
 struct WaveCounters {
     unsigned long long fetch;   // next ray index to hand out
@@ -293,6 +314,26 @@ struct WaveCounters {
     int dbg_src, dbg_lev, dbg_kind, dbg_leaf, dbg_prev;
     float dbg_d, dbg_te;
     unsigned long long dbg_pix;
+};
+
+// Device-resident state of one batch pipeline: the current wave's input
+// sizes and buffer parity, so that consecutive waves are enqueued without the
+// host reading counters in between.
+struct PipeDev {
+    long long nA, nB;         // current wave: implicit rays (seeds / children), explicit records
+    int kind;                 // 0 seeds, 1 children + explicit
+    int par;                  // input buffer parity
+    int src_lo, nb_src;       // batch of sources
+    int kstart;
+    int done;                 // batch finished (or stopped on an error)
+    long long peak;           // largest wave of the batch
+    int waves;                // waves run
+    int max_waves;
+    long long hc;             // merge table size of the current wave
+    int flush;                // record buffer flush requested
+    int pad;
+    unsigned long long peak_rec;  // most deposit records seen at a flush check
+    WaveCounters wc;
 };
 
 }  // namespace dartray

@@ -172,7 +172,11 @@ std::string build_topology(const int32_t nroot[3], const double root_lo[3], doub
                 q[a] = side ? static_cast<double>(b[a]) + b[3] : static_cast<double>(b[a]);
                 s[a] = side ? 1 : -1;
                 const int64_t nb = w.find(q, s, b[3]);
-                t->leaf_rope[6 * lf + 2 * a + side] = static_cast<int32_t>(nb);
+                // a leaf neighbour is stored as -(leaf + 2) so the marcher can
+                // use its box directly; a refined neighbour as its node id
+                int32_t code = kRopeBoundary;
+                if (nb >= 0) code = first_child[nb] < 0 ? -(leaf_of_node[nb] + 2) : static_cast<int32_t>(nb);
+                t->leaf_rope[6 * lf + 2 * a + side] = code;
             }
         }
     }

@@ -8,6 +8,8 @@
 
 namespace dartray {
 
+constexpr int32_t kRopeBoundary = -1;
+
 struct HostTopo {
     // node_child[node] = first child (>= 0) or -(leaf + 1) for a leaf
     std::vector<int32_t> node_child;
@@ -15,8 +17,9 @@ struct HostTopo {
     std::vector<float> node_box;   // [n_nodes * 4]
     std::vector<float> leaf_box;   // [n_leaf * 4]
     std::vector<int32_t> leaf_node;
-    // leaf_rope[leaf * 6 + 2 * axis + (side > 0)]: the node on the other side
-    // of that face, of the same or larger size, or -1 on the model boundary
+    // leaf_rope[leaf * 6 + 2 * axis + (side > 0)]: what lies beyond that face,
+    // of the same or larger size: a leaf as -(leaf + 2), a refined node as its
+    // node id, or kRopeBoundary on the model boundary
     std::vector<int32_t> leaf_rope;
     int max_depth = 0;
 };

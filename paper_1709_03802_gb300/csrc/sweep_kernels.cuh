@@ -13,23 +13,19 @@ constexpr int kBlock = 256;
 constexpr int kPixTab = 1020;  // pixel centres of levels 0..3 (j_sca levels)
 
 struct MarchArgs {
-    // wave input: [0, nA) implicit (seeds of sources src_lo.., or the 4 children
-    // of each high-list parent), [nA, nA + nB) explicit records
-    int wave_kind;  // 0 seeds, 1 children + explicit
-    long long nA, nB;
-    const RayRec *H_in;
-    const float *H_in_I;
-    const RayRec *M_in;
-    const float *M_in_I;
-    int kstart;
-    int src_lo;
+    // wave input (read from the pipeline state at launch): [0, nA) implicit
+    // (seeds of sources src_lo.., or the 4 children of each high-list parent),
+    // [nA, nA + nB) explicit records; buffers alternate by parity
+    PipeDev *pd;
+    RayRec *Hb[2];
+    float *HIb[2];
+    RayRec *Mb[2];
+    float *MIb[2];
     const int *src_leaf;     // source cell (or the leaf holding a point source)
     const int *src_hint;     // start leaf of the seeds (-1: locate)
     const float4 *src_pos;   // source position
     const float *src_S;      // [n_src][nl] per-sr luminosity (direct light)
     // outputs
-    RayRec *H_out;
-    float *H_out_I;
     RayRec *L_out;
     float *L_out_I;
     long long cap;           // records per queue (I arrays are [nl][cap])
@@ -42,7 +38,6 @@ struct MarchArgs {
     double split_c, merge_c; // 4 pi N_rays, 4 pi N_rays^max
     float split_cf, merge_cf;
     int k_ray_max, merge, max_cross;
-    WaveCounters *wc;
     DevStats *st;
     // deferred j_sca deposit: one record per depositing crossing (cell, ray
     // direction, scattered luminosity / HG row sum per wavelength)
@@ -132,7 +127,11 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
     __syncthreads();
 
     const int lane = threadIdx.x & (kWarp - 1);
-    const long long n_total = A.nA + A.nB;
+    PipeDev *pd = A.pd;
+    if (pd->done) return;  // uniform: the batch has no more rays
+    const long long nA = pd->nA, n_total = pd->nA + pd->nB;
+    const int par = pd->par, wave_kind = pd->kind, kstart = pd->kstart, src_lo = pd->src_lo;
+    WaveCounters *wc = &pd->wc;
     float hgB[NL], hgC[NL], alb[NL];
     int npx[NL], pixbase[NL];
 #pragma unroll
@@ -168,7 +167,7 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
         if (idle) {
             const int leader = __ffs(idle) - 1;
             unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(&A.wc->fetch, static_cast<unsigned long long>(__popc(idle)));
+            if (lane == leader) base = atomicAdd(&wc->fetch, static_cast<unsigned long long>(__popc(idle)));
             base = __shfl_sync(kFull, base, leader);
             if (!active) {
                 const long long idx = static_cast<long long>(base + __popc(idle & ((1u << lane) - 1u)));
@@ -183,12 +182,16 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                     supp = 0.f;
                     entry_axis = -1;
                     entry_coord = 0.f;
-                    if (idx < A.nA) {
-                        if (A.wave_kind == 0) {
-                            const long long npix0 = 12ll << (2 * A.kstart);
-                            src = A.src_lo + static_cast<int>(idx / npix0);
-                            pix = static_cast<unsigned long long>(idx % npix0);
-                            lev = A.kstart;
+                    if (idx < nA) {
+                        if (wave_kind == 0) {
+                            // idx < 2^32 (waves are bounded by the queues): 32-bit
+                            // arithmetic, division by the constant 12
+                            const unsigned u = static_cast<unsigned>(idx);
+                            const unsigned hi = u >> (2 * kstart), lo = u & ((1u << (2 * kstart)) - 1u);
+                            const unsigned s12 = hi / 12u;
+                            src = src_lo + static_cast<int>(s12);
+                            pix = (static_cast<unsigned long long>(hi - 12u * s12) << (2 * kstart)) | lo;
+                            lev = kstart;
                             kind = kSeed;
                             d = 0.f;
                             hint = A.src_hint[src];
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                             led.add(sh_led, LG_EMITTED, emit, om);
                         } else {
                             const long long pi_ = idx >> 2;
-                            const RayRec r = A.H_in[pi_];
+                            const RayRec r = A.Hb[par][pi_];
                             src = r.src;
                             lev = rr_lev(r.meta) + 1;
                             pix = r.pix * 4ull + static_cast<unsigned long long>(idx & 3);
@@ -222,11 +225,11 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                             par_pix = r.pix;
                             par_leaf = r.hint;  // the cell the parent split in
 #pragma unroll
-                            for (int l = 0; l < NL; ++l) I[l] = A.H_in_I[l * A.cap + pi_];
+                            for (int l = 0; l < NL; ++l) I[l] = A.HIb[par][l * A.cap + pi_];
                         }
                     } else {
-                        const long long mi = idx - A.nA;
-                        const RayRec r = A.M_in[mi];
+                        const long long mi = idx - nA;
+                        const RayRec r = A.Mb[par][mi];
                         src = r.src;
                         lev = rr_lev(r.meta);
                         kind = rr_kind(r.meta);
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                             entry_coord = r.plane;
                         }
 #pragma unroll
-                        for (int l = 0; l < NL; ++l) I[l] = A.M_in_I[l * A.cap + mi];
+                        for (int l = 0; l < NL; ++l) I[l] = A.MIb[par][l * A.cap + mi];
                     }
                     const float4 sp = A.src_pos[src];
                     xs = make_float3(sp.x, sp.y, sp.z);
@@ -337,10 +340,10 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                 ++c_escape;
                 outcome = 1;
             } else if (++ncross > A.max_cross) {
-                atomicOr(&A.wc->status, ST_CROSS_CAP);
-                if (atomicCAS(&A.wc->dbg_set, 0, 1) == 0) {
-                    A.wc->dbg_src = src; A.wc->dbg_lev = lev; A.wc->dbg_kind = kind; A.wc->dbg_leaf = leaf;
-                    A.wc->dbg_pix = pix; A.wc->dbg_d = d; A.wc->dbg_te = box.w; A.wc->dbg_prev = srcleaf;
+                atomicOr(&wc->status, ST_CROSS_CAP);
+                if (atomicCAS(&wc->dbg_set, 0, 1) == 0) {
+                    wc->dbg_src = src; wc->dbg_lev = lev; wc->dbg_kind = kind; wc->dbg_leaf = leaf;
+                    wc->dbg_pix = pix; wc->dbg_d = d; wc->dbg_te = box.w; wc->dbg_prev = srcleaf;
                 }
                 outcome = 1;
             } else {
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                 te = fminf(tx, fminf(ty, tz));
                 tie = (tx == te ? 1 : 0) | (ty == te ? 2 : 0) | (tz == te ? 4 : 0);
                 if (tie == 0) {  // non-finite direction: never expected, never indexed
-                    atomicOr(&A.wc->status, ST_NOPROGRESS);
+                    atomicOr(&wc->status, ST_NOPROGRESS);
                     active = false;
                 }
                 const float ds = fmaxf(te - d, 0.f);
@@ -459,21 +462,21 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
         // ------------------------------------------ high / low list appends
         {
             const bool wh = active && outcome == 2;
-            const unsigned long long slot = warp_append(wh, &A.wc->n_high, lane);
+            const unsigned long long slot = warp_append(wh, &wc->n_high, lane);
             if (wh) {
                 if (slot < static_cast<unsigned long long>(A.cap)) {
                     RayRec r;
                     r.pix = pix; r.src = src; r.d = d; r.hint = leaf; r.supp = 0.f; r.plane = entry_coord;
                     r.meta = rr_meta(lev, kind, entry_axis);
-                    A.H_out[slot] = r;
+                    A.Hb[1 - par][slot] = r;
 #pragma unroll
-                    for (int l = 0; l < NL; ++l) A.H_out_I[l * A.cap + slot] = I[l];
+                    for (int l = 0; l < NL; ++l) A.HIb[1 - par][l * A.cap + slot] = I[l];
                 } else {
-                    atomicOr(&A.wc->status, ST_QUEUE);
+                    atomicOr(&wc->status, ST_QUEUE);
                 }
             }
             const bool wl = active && outcome == 3;
-            const unsigned long long slot2 = warp_append(wl, &A.wc->n_low, lane);
+            const unsigned long long slot2 = warp_append(wl, &wc->n_low, lane);
             if (wl) {
                 if (slot2 < static_cast<unsigned long long>(A.cap)) {
                     RayRec r;
@@ -483,7 +486,7 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
 #pragma unroll
                     for (int l = 0; l < NL; ++l) A.L_out_I[l * A.cap + slot2] = I[l];
                 } else {
-                    atomicOr(&A.wc->status, ST_QUEUE);
+                    atomicOr(&wc->status, ST_QUEUE);
                 }
             }
         }
@@ -549,7 +552,9 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                     (tie & 1) ? bnd[0] : fminf(fmaxf(fmaf(te, n.x, xs.x), box.x), box.x + box.w),
                     (tie & 2) ? bnd[1] : fminf(fmaxf(fmaf(te, n.y, xs.y), box.y), box.y + box.w),
                     (tie & 4) ? bnd[2] : fminf(fmaxf(fmaf(te, n.z, xs.z), box.z), box.z + box.w));
-                const int nxt = next_leaf(G, leaf, tie, pe, n);
+                float4 nbox;
+                bool has_box;
+                const int nxt = next_leaf(G, leaf, tie, pe, n, &nbox, &has_box);
                 if (nxt < 0) {
                     float tmp[NL];
 #pragma unroll
@@ -558,11 +563,11 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                     ++c_escape;
                     outcome = 1;
                 } else if (nxt == leaf) {
-                    atomicOr(&A.wc->status, ST_NOPROGRESS);
+                    atomicOr(&wc->status, ST_NOPROGRESS);
                     outcome = 1;
                 } else {
                     leaf = nxt;
-                    box = __ldg(&G.leaf_box[leaf]);
+                    box = has_box ? nbox : __ldg(&G.leaf_box[leaf]);
 #pragma unroll
                     for (int l = 0; l < NL; ++l) {
                         kr[l] = __ldg(&G.kappa_rho[static_cast<long long>(leaf) * NL + l]);
@@ -602,17 +607,16 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
 
 // ------------------------------------------------------------------ merging
 struct MergeArgs {
+    PipeDev *pd;
     const RayRec *L;
     const float *L_I;
-    long long n_low;
     long long cap;
-    unsigned long long *hkey;  // [hcap], ~0 = empty
+    unsigned long long *hkey;  // ~0 = empty
     int *hcnt;
     int4 *hmem;
     long long hcap;
-    RayRec *M_out;
-    float *M_out_I;
-    WaveCounters *wc;
+    RayRec *Mb[2];
+    float *MIb[2];
     DevStats *st;
     int nl;
 };
@@ -631,80 +635,151 @@ __device__ inline unsigned long long hash64(unsigned long long k) {
     return k;
 }
 
+// Merge table size for the current wave: the power of two >= 2 n_low.
+__global__ void merge_size_kernel(PipeDev *pd, long long hcap) {
+    if (pd->done) return;
+    const unsigned long long nl = pd->wc.n_low;
+    long long hc = 0;
+    if (nl > 0) {
+        hc = 1;
+        while (hc < 2 * static_cast<long long>(nl)) hc <<= 1;
+        if (hc > hcap) {
+            atomicOr(&pd->wc.status, ST_QUEUE);
+            hc = 0;
+        }
+    }
+    pd->hc = hc;
+}
+
+__global__ void merge_clear_kernel(const MergeArgs A) {
+    const PipeDev *pd = A.pd;
+    if (pd->done) return;
+    const long long hc = pd->hc;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < hc;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        A.hkey[i] = ~0ull;
+        A.hcnt[i] = 0;
+    }
+}
+
 // Group low-list rays by (source, level, parent pixel).
 __global__ void merge_insert_kernel(const MergeArgs A) {
-    const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-    if (i >= A.n_low) return;
-    const unsigned long long key = merge_key(A.L[i]);
-    unsigned long long h = hash64(key) & static_cast<unsigned long long>(A.hcap - 1);
-    for (long long probe = 0; probe < A.hcap; ++probe) {
-        const unsigned long long prev = atomicCAS(&A.hkey[h], ~0ull, key);
-        if (prev == ~0ull || prev == key) {
-            const int c = atomicAdd(&A.hcnt[h], 1);
-            if (c < 4) reinterpret_cast<int *>(&A.hmem[h])[c] = static_cast<int>(i);
-            else atomicOr(&A.wc->status, ST_MERGE);
-            return;
+    PipeDev *pd = A.pd;
+    if (pd->done) return;
+    const long long hc = pd->hc;
+    const long long n_low = hc > 0 ? static_cast<long long>(min(pd->wc.n_low, static_cast<unsigned long long>(A.cap))) : 0;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n_low;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const unsigned long long key = merge_key(A.L[i]);
+        unsigned long long h = hash64(key) & static_cast<unsigned long long>(hc - 1);
+        bool placed = false;
+        for (long long probe = 0; probe < hc && !placed; ++probe) {
+            const unsigned long long prev = atomicCAS(&A.hkey[h], ~0ull, key);
+            if (prev == ~0ull || prev == key) {
+                const int c = atomicAdd(&A.hcnt[h], 1);
+                if (c < 4) reinterpret_cast<int *>(&A.hmem[h])[c] = static_cast<int>(i);
+                else atomicOr(&pd->wc.status, ST_MERGE);
+                placed = true;
+            }
+            h = (h + 1) & static_cast<unsigned long long>(hc - 1);
         }
-        h = (h + 1) & static_cast<unsigned long long>(A.hcap - 1);
+        if (!placed) atomicOr(&pd->wc.status, ST_MERGE);
     }
-    atomicOr(&A.wc->status, ST_MERGE);
 }
 
 // Eq. 3 / Fig. 1: four siblings that stopped on the same grid plane become
 // their parent ray with the mean intensity at the mean distance; the others
 // resume where they stopped with the merge test suppressed until the cell
-// size changes.
+// size changes.  Output: the explicit records of the next wave.
 __global__ void merge_emit_kernel(const MergeArgs A) {
-    const long long h = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-    if (h >= A.hcap || A.hkey[h] == ~0ull) return;
-    const int c = min(A.hcnt[h], 4);
-    int mem[4];
-    const int4 hm = A.hmem[h];
-    mem[0] = hm.x; mem[1] = hm.y; mem[2] = hm.z; mem[3] = hm.w;
-    bool ok = (A.hcnt[h] == 4);
-    if (ok) {
-        // order the siblings by pixel (sums in a fixed order)
-        for (int a = 0; a < 4; ++a)
-            for (int b = a + 1; b < 4; ++b)
-                if (A.L[mem[b]].pix < A.L[mem[a]].pix) { const int t = mem[a]; mem[a] = mem[b]; mem[b] = t; }
-        const RayRec &r0 = A.L[mem[0]];
-        for (int a = 1; a < 4; ++a) {
-            const RayRec &ra = A.L[mem[a]];
-            ok = ok && rr_axis(ra.meta) == rr_axis(r0.meta) && ra.plane == r0.plane;
+    PipeDev *pd = A.pd;
+    if (pd->done) return;
+    const long long hc = pd->hc;
+    RayRec *M_out = A.Mb[1 - pd->par];
+    float *M_out_I = A.MIb[1 - pd->par];
+    for (long long h = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; h < hc;
+         h += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (A.hkey[h] == ~0ull) continue;
+        const int c = min(A.hcnt[h], 4);
+        int mem[4];
+        const int4 hm = A.hmem[h];
+        mem[0] = hm.x; mem[1] = hm.y; mem[2] = hm.z; mem[3] = hm.w;
+        bool ok = (A.hcnt[h] == 4);
+        if (ok) {
+            // order the siblings by pixel (sums in a fixed order)
+            for (int a = 0; a < 4; ++a)
+                for (int b = a + 1; b < 4; ++b)
+                    if (A.L[mem[b]].pix < A.L[mem[a]].pix) { const int t = mem[a]; mem[a] = mem[b]; mem[b] = t; }
+            const RayRec &r0 = A.L[mem[0]];
+            for (int a = 1; a < 4; ++a) {
+                const RayRec &ra = A.L[mem[a]];
+                ok = ok && rr_axis(ra.meta) == rr_axis(r0.meta) && ra.plane == r0.plane;
+            }
+        }
+        if (ok) {
+            const unsigned long long slot = atomicAdd(&pd->wc.n_next, 1ull);
+            if (slot >= static_cast<unsigned long long>(A.cap)) { atomicOr(&pd->wc.status, ST_QUEUE); continue; }
+            const RayRec &r0 = A.L[mem[0]];
+            RayRec m;
+            m.pix = r0.pix >> 2;
+            m.src = r0.src;
+            float dsum = 0.f;
+            for (int a = 0; a < 4; ++a) dsum += A.L[mem[a]].d;
+            m.d = dsum * 0.25f;
+            m.hint = -1;
+            m.supp = 0.f;
+            m.plane = 0.f;
+            m.meta = rr_meta(rr_lev(r0.meta) - 1, kMerged, -1);
+            M_out[slot] = m;
+            for (int l = 0; l < A.nl; ++l) {
+                float sum = 0.f;
+                for (int a = 0; a < 4; ++a) sum += A.L_I[l * A.cap + mem[a]];
+                M_out_I[l * A.cap + slot] = sum * 0.25f;
+            }
+            atomicAdd(&A.st->cnt[CT_MERGE], 1ull);
+        } else {
+            const unsigned long long slot = atomicAdd(&pd->wc.n_next, static_cast<unsigned long long>(c));
+            if (slot + c > static_cast<unsigned long long>(A.cap)) { atomicOr(&pd->wc.status, ST_QUEUE); continue; }
+            for (int a = 0; a < c; ++a) {
+                RayRec r = A.L[mem[a]];
+                r.meta = rr_meta(rr_lev(r.meta), kResumed, rr_axis(r.meta));
+                // r.hint (stop leaf) and r.supp (its side) were set by the marcher
+                M_out[slot + a] = r;
+                for (int l = 0; l < A.nl; ++l) M_out_I[l * A.cap + slot + a] = A.L_I[l * A.cap + mem[a]];
+            }
+            atomicAdd(&A.st->cnt[CT_RESUME], static_cast<unsigned long long>(c));
         }
     }
-    if (ok) {
-        const unsigned long long slot = atomicAdd(&A.wc->n_next, 1ull);
-        if (slot >= static_cast<unsigned long long>(A.cap)) { atomicOr(&A.wc->status, ST_QUEUE); return; }
-        const RayRec &r0 = A.L[mem[0]];
-        RayRec m;
-        m.pix = r0.pix >> 2;
-        m.src = r0.src;
-        float dsum = 0.f;
-        for (int a = 0; a < 4; ++a) dsum += A.L[mem[a]].d;
-        m.d = dsum * 0.25f;
-        m.hint = -1;
-        m.supp = 0.f;
-        m.plane = 0.f;
-        m.meta = rr_meta(rr_lev(r0.meta) - 1, kMerged, -1);
-        A.M_out[slot] = m;
-        for (int l = 0; l < A.nl; ++l) {
-            float s = 0.f;
-            for (int a = 0; a < 4; ++a) s += A.L_I[l * A.cap + mem[a]];
-            A.M_out_I[l * A.cap + slot] = s * 0.25f;
-        }
-        atomicAdd(&A.st->cnt[CT_MERGE], 1ull);
-    } else {
-        const unsigned long long slot = atomicAdd(&A.wc->n_next, static_cast<unsigned long long>(c));
-        if (slot + c > static_cast<unsigned long long>(A.cap)) { atomicOr(&A.wc->status, ST_QUEUE); return; }
-        for (int a = 0; a < c; ++a) {
-            RayRec r = A.L[mem[a]];
-            r.meta = rr_meta(rr_lev(r.meta), kResumed, rr_axis(r.meta));
-            // r.hint (stop leaf) and r.supp (its side) were set by the marcher
-            A.M_out[slot + a] = r;
-            for (int l = 0; l < A.nl; ++l) A.M_out_I[l * A.cap + slot + a] = A.L_I[l * A.cap + mem[a]];
-        }
-        atomicAdd(&A.st->cnt[CT_RESUME], static_cast<unsigned long long>(c));
+}
+
+// End of a wave: the next wave consists of the four children of every
+// high-list parent (implicit) and the merged / resumed records (explicit).
+__global__ void wave_advance_kernel(PipeDev *pd) {
+    if (pd->done) return;
+    WaveCounters &w = pd->wc;
+    if (w.status) {  // stop the batch; the host reads the status
+        pd->done = 1;
+        return;
+    }
+    const long long na = 4 * static_cast<long long>(w.n_high), nb = static_cast<long long>(w.n_next);
+    pd->par ^= 1;
+    pd->nA = na;
+    pd->nB = nb;
+    pd->kind = 1;
+    w.fetch = 0;
+    w.n_high = 0;
+    w.n_low = 0;
+    w.n_next = 0;
+    pd->hc = 0;
+    if (na + nb == 0) {
+        pd->done = 1;
+        return;
+    }
+    pd->waves += 1;
+    if (na + nb > pd->peak) pd->peak = na + nb;
+    if (pd->waves > pd->max_waves) {
+        w.status |= ST_WAVE_CAP;
+        pd->done = 1;
     }
 }
 
@@ -736,8 +811,9 @@ __global__ void source_flags_kernel(const DevGrid G, int mode, const float *pend
 }
 
 // Block-level exclusive scan of flags -> per-block totals.
-__global__ void scan_blocks_kernel(const int *flags, int n, int *block_sum) {
+__global__ void scan_blocks_kernel(const PipeDev *pd, const int *flags, int n, int *block_sum) {
     __shared__ int sh[kBlock / kWarp];
+    if (pd && !pd->flush) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     int v = i < n ? flags[i] : 0;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -750,7 +826,8 @@ __global__ void scan_blocks_kernel(const int *flags, int n, int *block_sum) {
     }
 }
 
-__global__ void scan_offsets_kernel(int *block_sum, int nblocks, int *total) {
+__global__ void scan_offsets_kernel(const PipeDev *pd, int *block_sum, int nblocks, int *total) {
+    if (pd && !pd->flush) return;
     // single thread: fine for <= a few 10^4 blocks
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         int s = 0;
@@ -873,7 +950,9 @@ __global__ void rec_count_kernel(const unsigned *cell, long long n, unsigned *cn
 }
 
 // exclusive scan of per-cell counts: block totals, then per-element offsets
-__global__ void scan_apply_kernel(const unsigned *cnt, int n, const int *block_off, unsigned *off, unsigned *cur) {
+__global__ void scan_apply_kernel(const PipeDev *pd, const unsigned *cnt, int n, const int *block_off, unsigned *off,
+                                  unsigned *cur) {
+    if (pd && !pd->flush) return;
     __shared__ unsigned sh[kBlock / kWarp];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -893,9 +972,26 @@ __global__ void scan_apply_kernel(const unsigned *cnt, int n, const int *block_o
     }
 }
 
-__global__ void rec_scatter_kernel(const unsigned *cell, const float4 *dir, const float *coef, long long n,
-                                   long long cap, int nl, unsigned *cur, unsigned *scell, float4 *sdir,
-                                   float *scoef) {
+// The flush runs when the pipeline's record buffer is half full (or when the
+// host forces it); every flush kernel reads the decision and the record count
+// from device memory.
+__global__ void flush_decide_kernel(PipeDev *pd, const unsigned long long *rec_n, long long rec_cap, int force) {
+    const unsigned long long n = *rec_n;
+    if (n > pd->peak_rec) pd->peak_rec = n;
+    pd->flush = (n > 0 && (force || static_cast<long long>(n) >= rec_cap / 2)) ? 1 : 0;
+}
+
+__global__ void flush_reset_kernel(PipeDev *pd, unsigned long long *rec_n, unsigned *cnt, int n_leaf) {
+    if (!pd->flush) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_leaf; i += gridDim.x * blockDim.x) cnt[i] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *rec_n = 0;
+}
+
+__global__ void rec_scatter_kernel(const PipeDev *pd, const unsigned long long *rec_n, const unsigned *cell,
+                                   const float4 *dir, const float *coef, long long cap, int nl, unsigned *cur,
+                                   unsigned *scell, float4 *sdir, float *scoef) {
+    if (!pd->flush) return;
+    const long long n = static_cast<long long>(min(*rec_n, static_cast<unsigned long long>(cap)));
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
         const unsigned c = cell[i];
@@ -1006,11 +1102,14 @@ __device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, 
 }
 
 template <int PPL>
-__global__ void __launch_bounds__(kBlock) cell_accumulate_kernel(const DevGrid G, int l, long long n,
+__global__ void __launch_bounds__(kBlock) cell_accumulate_kernel(const DevGrid G, int l, const PipeDev *pd,
+                                                                 const unsigned long long *rec_n,
                                                                  const unsigned *scell, const float4 *sdir,
                                                                  const float *scoef, long long cap, float *pend) {
     __shared__ float4 sh_rec[kBlock / kWarp][kWarp];
     __shared__ unsigned sh_cell[kBlock / kWarp][kWarp];
+    if (!pd->flush) return;
+    const long long n = static_cast<long long>(min(*rec_n, static_cast<unsigned long long>(cap)));
     const int lane = threadIdx.x & 31;
     const long long warps = static_cast<long long>(gridDim.x) * (blockDim.x / kWarp);
     const long long nranges = (n + kAccRange - 1) / kAccRange;
