@@ -974,7 +974,7 @@ int dartray_map(dartray_grid *g, const double observer[3], int32_t nside_k, int3
     if (!dst_is_device) CK(cudaMalloc(reinterpret_cast<void **>(&dst), nmap * sizeof(float)));
     CK(cudaMemsetAsync(dst, 0, nmap * sizeof(float), g->stream));
     MapArgs M{};
-    for (int a = 0; a < 3; ++a) M.obs[a] = static_cast<float>(observer[a]);
+    for (int a = 0; a < 3; ++a) M.obs[a] = observer[a];  // double: exact subdivision / pixel decisions
     M.nside_k = nside_k;
     M.max_sub = max_sub;
     M.jsca = use_jsca ? g->d_jtot : nullptr;
