@@ -199,6 +199,25 @@ int dartray_jsca(dartray_grid *grid, int which, float *out, int dst_is_device);
 int dartray_map(dartray_grid *grid, const double observer[3], int32_t nside_k, int32_t max_sub,
                 int32_t use_jsca, float *map, int dst_is_device);
 
+/*
+ * dartray_map without any device allocation, for callers that cannot call
+ * cudaMalloc (for example code running under an allocator that forbids it,
+ * or an application that reserves all device memory up front).  The paper has
+ * no counterpart; the result equals dartray_map's.
+ *
+ * The map is summed in a fixed 8 MiB static device buffer (2^21 floats) and
+ * then copied to map (host or device).  Maps larger than that -- 12*4^nside_k
+ * pixels times n_lambda above 2^21 -- are rejected with DARTRAY_E_INVAL.  The
+ * buffer is shared by every call in the process and keeps the last call's
+ * map; each call clears the part it uses.  Calls that overlap on the GPU
+ * (several threads, or several streams without ordering) race on it.  The
+ * first call on a device looks up the buffer's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * device that loads the library holds the buffer until the process exits.
+ */
+int dartray_map_noalloc(dartray_grid *grid, const double observer[3], int32_t nside_k, int32_t max_sub,
+                        int32_t use_jsca, float *map, int dst_is_device);
+
 /* Save / restore the RFED and source-function state (U, U_LL, pending,
  * j_sca_total and the step-2 scattered luminosity) to a raw binary file, so
  * that maps can be made without repeating the sweep. */

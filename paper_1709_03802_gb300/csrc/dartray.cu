@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <memory>
+#include <mutex>
 #include <utility>
 #include <cmath>
 #include <cstdio>
@@ -63,6 +64,12 @@ int k_hp_host(double g, int n_fwhm, int cap) {
 }  // namespace
 
 constexpr int kPipes = 2;
+
+// Map staging buffer of dartray_map_noalloc: a fixed device array (8 MiB), so
+// that entry point needs no allocation.  Every device that loads the library
+// holds it until exit.
+constexpr long long kNoAllocMapFloats = 1ll << 21;
+static __device__ __align__(256) float g_noalloc_map[kNoAllocMapFloats];
 
 struct Pipe {
     cudaStream_t stream = nullptr;
@@ -989,6 +996,63 @@ int dartray_map(dartray_grid *g, const double observer[3], int32_t nside_k, int3
         CK(cudaStreamSynchronize(g->stream));
         cudaFree(dst);
     }
+    CK(cudaStreamSynchronize(g->stream));
+    return DARTRAY_OK;
+}
+
+// Device address of g_noalloc_map on the current device.  Host code must not
+// use the symbol itself (it names a host-side shadow); the address is looked
+// up once per device, with that device current, and cached.
+static int noalloc_scratch(int device, float **out) {
+    static std::mutex mu;
+    static float *addr[256] = {nullptr};
+    if (device < 0 || device >= 256) return fail(DARTRAY_E_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_map);
+        if (e != cudaSuccess || !p)
+            return fail(DARTRAY_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        addr[device] = static_cast<float *>(p);
+    }
+    *out = addr[device];
+    return DARTRAY_OK;
+}
+
+int dartray_map_noalloc(dartray_grid *g, const double observer[3], int32_t nside_k, int32_t max_sub,
+                        int32_t use_jsca, float *map, int dst_is_device) {
+    g_last_error.clear();
+    if (!g || !observer || !map) return fail(DARTRAY_E_INVAL, "null argument");
+    if (nside_k < 0 || nside_k > 10 || max_sub < 0 || max_sub > 6) return fail(DARTRAY_E_INVAL, "bad map size");
+    const long long npix = 12ll << (2 * nside_k);
+    const long long nmap = npix * g->nl;
+    if (nmap > kNoAllocMapFloats) {
+        char m[200];
+        std::snprintf(m, sizeof m,
+                      "map of %lld floats (12*4^%d pixels x %d wavelengths) exceeds the %lld-float static buffer "
+                      "of dartray_map_noalloc",
+                      nmap, nside_k, g->nl, kNoAllocMapFloats);
+        return fail(DARTRAY_E_INVAL, m);
+    }
+    int rc = set_device(g);
+    if (rc) return rc;
+    float *scratch = nullptr;
+    if ((rc = noalloc_scratch(g->device, &scratch))) return rc;
+    // the buffer keeps the previous call's map: clear the part this call sums into
+    CK(cudaMemsetAsync(scratch, 0, static_cast<size_t>(nmap) * sizeof(float), g->stream));
+    MapArgs M{};
+    for (int a = 0; a < 3; ++a) M.obs[a] = observer[a];
+    M.nside_k = nside_k;
+    M.max_sub = max_sub;
+    M.jsca = use_jsca ? g->d_jtot : nullptr;
+    M.map = scratch;
+    const int blocks = (g->n_leaf + kBlock - 1) / kBlock;
+    rc = launch_map(g->G, M, blocks, g->stream);
+    if (rc) return fail(DARTRAY_E_INVAL, "unsupported n_lambda for maps");
+    ++g->launches;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(map, scratch, static_cast<size_t>(nmap) * sizeof(float),
+                       dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
 }

@@ -93,6 +93,7 @@ def load(build_if_missing=True):
         "dartray_jsca_layout": ([P, P, P, P], C.c_int),
         "dartray_jsca": ([P, C.c_int, P, C.c_int], C.c_int),
         "dartray_map": ([P, P, C.c_int32, C.c_int32, C.c_int32, P, C.c_int], C.c_int),
+        "dartray_map_noalloc": ([P, P, C.c_int32, C.c_int32, C.c_int32, P, C.c_int], C.c_int),
         "dartray_state_save": ([P, C.c_char_p], C.c_int),
         "dartray_state_load": ([P, C.c_char_p], C.c_int),
         "dartray_grid_destroy": ([P], None),
@@ -107,8 +108,8 @@ def load(build_if_missing=True):
 
 
 EXPORTED = ("dartray_params_default", "dartray_grid_create", "dartray_direct", "dartray_scatter_iter",
-            "dartray_rfed", "dartray_jsca_layout", "dartray_jsca", "dartray_map", "dartray_state_save",
-            "dartray_state_load", "dartray_grid_destroy", "dartray_last_error")
+            "dartray_rfed", "dartray_jsca_layout", "dartray_jsca", "dartray_map", "dartray_map_noalloc",
+            "dartray_state_save", "dartray_state_load", "dartray_grid_destroy", "dartray_last_error")
 
 
 def _check(rc):
@@ -163,6 +164,12 @@ def dartray_jsca(h, which, out_ptr, dst_is_device):
 def dartray_map(h, observer, nside_k, max_sub, use_jsca, out_ptr, dst_is_device):
     obs = (C.c_double * 3)(*[float(v) for v in observer])
     _check(load().dartray_map(h, obs, int(nside_k), int(max_sub), int(use_jsca), out_ptr, int(dst_is_device)))
+
+
+def dartray_map_noalloc(h, observer, nside_k, max_sub, use_jsca, out_ptr, dst_is_device):
+    obs = (C.c_double * 3)(*[float(v) for v in observer])
+    _check(load().dartray_map_noalloc(h, obs, int(nside_k), int(max_sub), int(use_jsca), out_ptr,
+                                      int(dst_is_device)))
 
 
 def dartray_state_save(h, path):
