@@ -240,16 +240,33 @@ __device__ inline int locate_root(const DevGrid &G, const float3 p, const float3
 // Face links: >= 0 a refined node, -1 the model boundary, <= -2 a leaf
 // (-(leaf + 2)).  On return *box holds the new leaf's box when the link led
 // straight to a leaf (has_box = true).
-__device__ inline int next_leaf(const DevGrid &G, int leaf, int tie, const float3 pe, const float3 n, float4 *box,
-                                bool *has_box) {
-    const int a = __ffs(tie) - 1;
-    const float na = a == 0 ? n.x : (a == 1 ? n.y : n.z);
-    const int nb = __ldg(&G.leaf_rope[6 * leaf + 2 * a + (na > 0.f ? 1 : 0)]);
+// Face link codes (built on the host): >= 0 a refined node; -1 the model
+// boundary; -(leaf + 2) a larger leaf; -(2^30) - leaf a leaf of the same size.
+constexpr int kLinkSameSize = -(1 << 30);
+
+// Follow the face link `code` of exit axis a out of the leaf with box cur to
+// the leaf holding the exit point pe.  When the link leads straight to a leaf
+// its box is returned in *box (computed for a same-size neighbour) and
+// *has_box is set.
+__device__ inline int follow_link(const DevGrid &G, int code, int a, const float4 cur, const float3 pe,
+                                  const float3 n, float4 *box, bool *has_box) {
     *has_box = false;
-    if (nb == -1) return -1;
-    if (nb <= -2) {
-        const int lf = -nb - 2;
-        const float4 b = __ldg(&G.leaf_box[lf]);
+    if (code == -1) return -1;
+    if (code < 0) {
+        int lf;
+        float4 b;
+        if (code <= kLinkSameSize) {
+            lf = kLinkSameSize - code;
+            b = cur;
+            const float na = a == 0 ? n.x : (a == 1 ? n.y : n.z);
+            const float sh = na > 0.f ? cur.w : -cur.w;
+            if (a == 0) b.x += sh;
+            else if (a == 1) b.y += sh;
+            else b.z += sh;
+        } else {
+            lf = -code - 2;
+            b = __ldg(&G.leaf_box[lf]);
+        }
         if (inside_box(b, pe, n)) {
             *box = b;
             *has_box = true;
@@ -257,15 +274,18 @@ __device__ inline int next_leaf(const DevGrid &G, int leaf, int tie, const float
         }
         return locate_root(G, pe, n);
     }
-    const float4 b = __ldg(&G.node_box[nb]);
-    if (inside_box(b, pe, n)) return descend(G, nb, b, pe, n);
+    const float4 b = __ldg(&G.node_box[code]);
+    if (inside_box(b, pe, n)) return descend(G, code, b, pe, n);
     return locate_root(G, pe, n);
 }
 
 __device__ inline int next_leaf(const DevGrid &G, int leaf, int tie, const float3 pe, const float3 n) {
+    const int a = __ffs(tie) - 1;
+    const float na = a == 0 ? n.x : (a == 1 ? n.y : n.z);
+    const int code = __ldg(&G.leaf_rope[6 * leaf + 2 * a + (na > 0.f ? 1 : 0)]);
     float4 b;
     bool hb;
-    return next_leaf(G, leaf, tie, pe, n, &b, &hb);
+    return follow_link(G, code, a, __ldg(&G.leaf_box[leaf]), pe, n, &b, &hb);
 }
 
 // ------------------------------------------------------------------ rays

@@ -157,6 +157,7 @@ std::string build_topology(const int32_t nroot[3], const double root_lo[3], doub
             return msg;
         }
     if (nleaf_seen != n_leaf) return "leaf count does not match n_leaf";
+    if (n_leaf >= (1 << 29)) return "more than 2^29 leaves";
 
     // face links: for face (axis a, side s) of leaf box b, the node beyond the
     // face centre of size >= side (a coarser leaf or a same-size node)
@@ -175,7 +176,15 @@ std::string build_topology(const int32_t nroot[3], const double root_lo[3], doub
                 // a leaf neighbour is stored as -(leaf + 2) so the marcher can
                 // use its box directly; a refined neighbour as its node id
                 int32_t code = kRopeBoundary;
-                if (nb >= 0) code = first_child[nb] < 0 ? -(leaf_of_node[nb] + 2) : static_cast<int32_t>(nb);
+                if (nb >= 0) {
+                    if (first_child[nb] >= 0) {
+                        code = static_cast<int32_t>(nb);
+                    } else {
+                        const int32_t nl = leaf_of_node[nb];
+                        const bool same = t->node_box[4 * nb + 3] == b[3];
+                        code = same ? kRopeSameSize - nl : -(nl + 2);
+                    }
+                }
                 t->leaf_rope[6 * lf + 2 * a + side] = code;
             }
         }

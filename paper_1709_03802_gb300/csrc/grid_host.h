@@ -8,7 +8,11 @@
 
 namespace dartray {
 
+// Face link codes: >= 0 refined node id; -1 model boundary; -(leaf + 2) a
+// larger leaf; kRopeSameSize - leaf a leaf of the same size (its box is the
+// current box shifted by one side).  Leaf ids are below 2^29.
 constexpr int32_t kRopeBoundary = -1;
+constexpr int32_t kRopeSameSize = -(1 << 30);
 
 struct HostTopo {
     // node_child[node] = first child (>= 0) or -(leaf + 1) for a leaf
@@ -17,9 +21,8 @@ struct HostTopo {
     std::vector<float> node_box;   // [n_nodes * 4]
     std::vector<float> leaf_box;   // [n_leaf * 4]
     std::vector<int32_t> leaf_node;
-    // leaf_rope[leaf * 6 + 2 * axis + (side > 0)]: what lies beyond that face,
-    // of the same or larger size: a leaf as -(leaf + 2), a refined node as its
-    // node id, or kRopeBoundary on the model boundary
+    // leaf_rope[leaf * 6 + 2 * axis + (side > 0)]: what lies beyond that face
+    // (codes above)
     std::vector<int32_t> leaf_rope;
     int max_depth = 0;
 };

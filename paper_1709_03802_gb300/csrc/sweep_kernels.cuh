@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
         pixbase[l] = static_cast<int>(dir_tab_offset(G.k_lam[l]));
     }
 
-    bool active = false;
+    bool active = false, exhausted = false;
     int src = 0, lev = 0, kind = 0, leaf = -1, srcleaf = -1, ncross = 0, entry_axis = -1;
     unsigned long long pix = 0;
     float3 xs = make_float3(0, 0, 0), n = make_float3(0, 0, 1);
@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
     bool first = true, dyadic_src = true, need_z = false;
     float I[NL], Z[NL], acc_dep[NL], acc_skip[NL];
     float kr[NL], ull[NL];  // kappa*rho and U_LL of the current leaf (loaded with its box)
+    int link[3] = {-1, -1, -1};  // face links of the current leaf in the direction of travel
 #pragma unroll
     for (int l = 0; l < NL; ++l) { I[l] = 0.f; Z[l] = 1.f; acc_dep[l] = 0.f; acc_skip[l] = 0.f; }
     unsigned c_rays = 0, c_cross = 0, c_split = 0, c_block = 0, c_escape = 0, c_cut = 0, c_low = 0;
@@ -162,13 +163,16 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
 
     for (;;) {
         // ---------------------------------------------------------- fetch
+        // refill idle lanes once a quarter of the warp is idle (the ray setup
+        // is divergent; sharing it among more lanes costs fewer instructions)
         const unsigned idle = __ballot_sync(kFull, !active);
         bool started = false;
-        if (idle) {
+        if (!exhausted && (__popc(idle) >= 8 || idle == kFull)) {
             const int leader = __ffs(idle) - 1;
             unsigned long long base = 0;
             if (lane == leader) base = atomicAdd(&wc->fetch, static_cast<unsigned long long>(__popc(idle)));
             base = __shfl_sync(kFull, base, leader);
+            exhausted = base + __popc(idle) >= static_cast<unsigned long long>(n_total);
             if (!active) {
                 const long long idx = static_cast<long long>(base + __popc(idle & ((1u << lane) - 1u)));
                 if (idx < n_total) {
@@ -290,6 +294,9 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                             kr[l] = __ldg(&G.kappa_rho[static_cast<long long>(leaf) * NL + l]);
                             ull[l] = MODE == MODE_LL ? 0.f : __ldg(&A.U_LL[static_cast<long long>(leaf) * NL + l]);
                         }
+                        link[0] = __ldg(&G.leaf_rope[6 * leaf + (n.x > 0.f ? 1 : 0)]);
+                        link[1] = __ldg(&G.leaf_rope[6 * leaf + 2 + (n.y > 0.f ? 1 : 0)]);
+                        link[2] = __ldg(&G.leaf_rope[6 * leaf + 4 + (n.z > 0.f ? 1 : 0)]);
                     }
                     first = true;
                     ncross = 0;
@@ -554,7 +561,9 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                     (tie & 4) ? bnd[2] : fminf(fmaxf(fmaf(te, n.z, xs.z), box.z), box.z + box.w));
                 float4 nbox;
                 bool has_box;
-                const int nxt = next_leaf(G, leaf, tie, pe, n, &nbox, &has_box);
+                const int ea = __ffs(tie) - 1;
+                const int nxt = follow_link(G, ea == 0 ? link[0] : (ea == 1 ? link[1] : link[2]), ea, box, pe, n,
+                                            &nbox, &has_box);
                 if (nxt < 0) {
                     float tmp[NL];
 #pragma unroll
@@ -573,6 +582,9 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                         kr[l] = __ldg(&G.kappa_rho[static_cast<long long>(leaf) * NL + l]);
                         ull[l] = MODE == MODE_LL ? 0.f : __ldg(&A.U_LL[static_cast<long long>(leaf) * NL + l]);
                     }
+                    link[0] = __ldg(&G.leaf_rope[6 * leaf + (n.x > 0.f ? 1 : 0)]);
+                    link[1] = __ldg(&G.leaf_rope[6 * leaf + 2 + (n.y > 0.f ? 1 : 0)]);
+                    link[2] = __ldg(&G.leaf_rope[6 * leaf + 4 + (n.z > 0.f ? 1 : 0)]);
                     if (supp != 0.f && box.w != supp) supp = 0.f;
                     first = false;
                 }
@@ -987,18 +999,34 @@ __global__ void flush_reset_kernel(PipeDev *pd, unsigned long long *rec_n, unsig
     if (blockIdx.x == 0 && threadIdx.x == 0) *rec_n = 0;
 }
 
+// Bucket records by cell.  Consecutive records often share a cell (they come
+// from one warp of the marcher), so the lanes of a warp that hold the same
+// cell take their cursor positions with one atomic.
 __global__ void rec_scatter_kernel(const PipeDev *pd, const unsigned long long *rec_n, const unsigned *cell,
                                    const float4 *dir, const float *coef, long long cap, int nl, unsigned *cur,
                                    unsigned *scell, float4 *sdir, float *scoef) {
     if (!pd->flush) return;
     const long long n = static_cast<long long>(min(*rec_n, static_cast<unsigned long long>(cap)));
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const unsigned c = cell[i];
-        const unsigned pos = atomicAdd(&cur[c], 1u);
-        scell[pos] = c;
-        sdir[pos] = dir[i];
-        for (int l = 0; l < nl; ++l) scoef[l * cap + pos] = coef[l * cap + i];
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    // every lane of a warp runs the same number of iterations (warp-uniform
+    // bound) so the warp-wide match below is always converged
+    const long long warp0 = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) - lane;
+    for (long long w = warp0; w < n; w += stride) {
+        const long long i = w + lane;
+        const bool ok = i < n;
+        const unsigned c = ok ? cell[i] : 0xffffffffu;
+        const unsigned peers = __match_any_sync(kFull, c);
+        const int leader = __ffs(peers) - 1;
+        unsigned base = 0;
+        if (ok && lane == leader) base = atomicAdd(&cur[c], static_cast<unsigned>(__popc(peers)));
+        base = __shfl_sync(kFull, base, leader);
+        if (ok) {
+            const unsigned pos = base + __popc(peers & ((1u << lane) - 1u));
+            scell[pos] = c;
+            sdir[pos] = dir[i];
+            for (int l = 0; l < nl; ++l) scoef[l * cap + pos] = coef[l * cap + i];
+        }
     }
 }
 
@@ -1034,7 +1062,7 @@ __device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsig
 template <int PPL>
 __device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, long long end, const unsigned *scell,
                                         const float4 *sdir, const float *scoef, long long cap, float *pend,
-                                        int lane, float4 *sh_rec, unsigned *sh_cell) {
+                                        int lane, ulonglong2 *sh_rec, ulonglong2 *sh_rec2, unsigned *sh_cell) {
     constexpr int NP2 = (PPL + 1) / 2;
     const int k = G.k_lam[l];
     const int np = 12 << (2 * k);
@@ -1070,21 +1098,25 @@ __device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, 
     for (long long b = beg; b < end; b += kWarp) {
         const long long r = b + lane;
         if (r < end) {
+            // staged as duplicated pairs (x, x) so the loop below reads
+            // ready-made f32x2 operands
             const float4 dv = sdir[r];
-            sh_rec[lane] = make_float4(Cg * dv.x, Cg * dv.y, Cg * dv.z, scoef[l * cap + r]);
+            const float cf = scoef[l * cap + r];
+            sh_rec[lane] = make_ulonglong2(f2_pack(make_float2(Cg * dv.x, Cg * dv.x)),
+                                           f2_pack(make_float2(Cg * dv.y, Cg * dv.y)));
+            sh_rec2[lane] = make_ulonglong2(f2_pack(make_float2(Cg * dv.z, Cg * dv.z)), f2_pack(make_float2(cf, cf)));
             sh_cell[lane] = scell[r];
         }
         __syncwarp();
         const int cntj = static_cast<int>(min(static_cast<long long>(kWarp), end - b));
         for (int j = 0; j < cntj; ++j) {
-            const float4 rv = sh_rec[j];
+            const ulonglong2 ra = sh_rec[j], rb = sh_rec2[j];
             const unsigned cj = sh_cell[j];
             if (cj != cur) {
                 flush(cur);
                 cur = cj;
             }
-            const unsigned long long cx = f2_pack(make_float2(rv.x, rv.x)), cy = f2_pack(make_float2(rv.y, rv.y)),
-                                     cz = f2_pack(make_float2(rv.z, rv.z)), cc = f2_pack(make_float2(rv.w, rv.w));
+            const unsigned long long cx = ra.x, cy = ra.y, cz = rb.x, cc = rb.y;
 #pragma unroll
             for (int i = 0; i < NP2; ++i) {
                 unsigned long long t = f2_fma(mx[i], cx, B2);
@@ -1092,8 +1124,7 @@ __device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, 
                 t = f2_fma(mz[i], cz, t);
                 const float2 tv = f2_unpack(t);
                 const unsigned long long rr = f2_pack(make_float2(rsqrtf(tv.x), rsqrtf(tv.y)));
-                const unsigned long long r3 = f2_mul(f2_mul(rr, rr), rr);
-                acc[i] = f2_fma(cc, r3, acc[i]);
+                acc[i] = f2_fma(cc, f2_mul(f2_mul(rr, rr), rr), acc[i]);
             }
         }
         __syncwarp();
@@ -1106,7 +1137,8 @@ __global__ void __launch_bounds__(kBlock) cell_accumulate_kernel(const DevGrid G
                                                                  const unsigned long long *rec_n,
                                                                  const unsigned *scell, const float4 *sdir,
                                                                  const float *scoef, long long cap, float *pend) {
-    __shared__ float4 sh_rec[kBlock / kWarp][kWarp];
+    __shared__ ulonglong2 sh_rec[kBlock / kWarp][kWarp];
+    __shared__ ulonglong2 sh_rec2[kBlock / kWarp][kWarp];
     __shared__ unsigned sh_cell[kBlock / kWarp][kWarp];
     if (!pd->flush) return;
     const long long n = static_cast<long long>(min(*rec_n, static_cast<unsigned long long>(cap)));
@@ -1117,7 +1149,7 @@ __global__ void __launch_bounds__(kBlock) cell_accumulate_kernel(const DevGrid G
          w += warps) {
         const long long beg = w * kAccRange, end = min(n, beg + kAccRange);
         accumulate_range<PPL>(G, l, beg, end, scell, sdir, scoef, cap, pend, lane, sh_rec[threadIdx.x >> 5],
-                              sh_cell[threadIdx.x >> 5]);
+                              sh_rec2[threadIdx.x >> 5], sh_cell[threadIdx.x >> 5]);
     }
 }
 
