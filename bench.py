@@ -110,6 +110,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def max_over_ranks(value, dist, device):
+    """Largest value over the ranks of the process group (the job's time is
+    the slowest replica's); `dist` None means a single process."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all replicas per second of the slowest one."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def run_step(gpu, grid):
     """One pass of the hot path: steps 1-2, scattering iterations to f_L, map."""
     st = gpu.direct()
@@ -256,13 +272,9 @@ def main():
             total_ms += e0.elapsed_time(e1)
             results.append(r)
     clocks = clk.summary(local_rank)
-    ms = total_ms / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(total_ms / args.steps, dist, "cuda")
     cross = float(np.mean([r["crossings"] for r in results]))
-    value = cross * world / (ms / 1e3)
+    value = whole_job_rate(cross, world, ms)
     it_ms = [x for r in results for x in r["iter_ms"]]
     march_ms = sum(r["march_ms"] for r in results)
     nl = grid.n_lambda

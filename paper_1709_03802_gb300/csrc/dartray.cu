@@ -250,10 +250,10 @@ int enqueue_flush(dartray_grid *g, Pipe &P, float *pend_dst, int force) {
                                              g->nl, P.d_cur, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef);
     for (int l = 0; l < g->nl; ++l) {
         switch (g->k_lam[l]) {
-        case 0: cell_accumulate_kernel<1><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_rec_n, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
-        case 1: cell_accumulate_kernel<2><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_rec_n, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
-        case 2: cell_accumulate_kernel<6><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_rec_n, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
-        default: cell_accumulate_kernel<24><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_rec_n, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
+        case 0: cell_accumulate_kernel<1><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_total, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
+        case 1: cell_accumulate_kernel<2><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_total, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
+        case 2: cell_accumulate_kernel<6><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_total, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
+        default: cell_accumulate_kernel<24><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_total, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
         }
     }
     flush_reset_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, P.d_rec_n, P.d_cnt, g->n_leaf);

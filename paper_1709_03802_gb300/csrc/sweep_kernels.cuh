@@ -63,6 +63,44 @@ __device__ inline unsigned long long warp_append(bool want, unsigned long long *
     return base + __popc(m & ((1u << lane) - 1u));
 }
 
+// Output lists are filled in per-warp chunks: a warp reserves `chunk` slots
+// with one atomic and hands them out over many iterations, so appends rarely
+// wait on a returning atomic.  Slots a warp leaves unused are holes, marked
+// by the caller and skipped by the list's reader.
+struct ChunkState {
+    unsigned long long base;
+    unsigned left;
+    unsigned pad;
+};
+
+__device__ inline unsigned long long chunk_append(bool want, unsigned long long *counter, ChunkState *st,
+                                                  unsigned chunk, int lane, unsigned long long *hole_beg,
+                                                  unsigned *hole_n) {
+    const unsigned m = __ballot_sync(kFull, want);
+    *hole_n = 0;
+    if (!m) return 0;
+    const unsigned cnt = __popc(m);
+    unsigned long long base = st->base;
+    unsigned left = st->left;
+    if (cnt > left) {
+        *hole_beg = base;
+        *hole_n = left;
+        const unsigned take = max(chunk, cnt);
+        unsigned long long nb = 0;
+        if (lane == 0) nb = atomicAdd(counter, static_cast<unsigned long long>(take));
+        base = __shfl_sync(kFull, nb, 0);
+        left = take;
+    }
+    const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+    __syncwarp();
+    if (lane == 0) {
+        st->base = base + cnt;
+        st->left = left - cnt;
+    }
+    __syncwarp();
+    return slot;
+}
+
 // Luminosity ledger of a lane: float32 sums in registers (few wavelengths)
 // reduced in double across the warp once per launch, or (many wavelengths)
 // double atomics in shared memory per finished ray.
@@ -121,12 +159,19 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
     __shared__ float4 sh_pix[kPixTab];
     __shared__ double sh_led[LG_N][kMaxLambda];
     __shared__ unsigned long long sh_cnt[CT_N];
+    __shared__ ChunkState sh_chunk[kBlock / kWarp][3];  // high list, low list, deposit records
     for (int i = threadIdx.x; i < kPixTab; i += blockDim.x) sh_pix[i] = G.dirtab[i];
     for (int i = threadIdx.x; i < LG_N * kMaxLambda; i += blockDim.x) (&sh_led[0][0])[i] = 0.0;
     if (threadIdx.x < CT_N) sh_cnt[threadIdx.x] = 0;
+    if (threadIdx.x < (kBlock / kWarp) * 3) {
+        ChunkState &c = (&sh_chunk[0][0])[threadIdx.x];
+        c.base = 0;
+        c.left = 0;
+    }
     __syncthreads();
 
     const int lane = threadIdx.x & (kWarp - 1);
+    ChunkState *chunks = sh_chunk[threadIdx.x >> 5];
     PipeDev *pd = A.pd;
     if (pd->done) return;  // uniform: the batch has no more rays
     const long long nA = pd->nA, n_total = pd->nA + pd->nB;
@@ -179,6 +224,7 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                     started = true;
                     active = true;
                     int hint = -1;
+                    bool hole = false;
                     int par_axis = -1;
                     float par_coord = 0.f;
                     unsigned long long par_pix = 0;
@@ -219,7 +265,8 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                         } else {
                             const long long pi_ = idx >> 2;
                             const RayRec r = A.Hb[par][pi_];
-                            src = r.src;
+                            hole = r.src < 0;  // unused slot of a warp's chunk
+                            src = hole ? 0 : r.src;
                             lev = rr_lev(r.meta) + 1;
                             pix = r.pix * 4ull + static_cast<unsigned long long>(idx & 3);
                             kind = kChild;
@@ -248,6 +295,10 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
 #pragma unroll
                         for (int l = 0; l < NL; ++l) I[l] = A.MIb[par][l * A.cap + mi];
                     }
+                    if (hole) {
+                        active = false;
+                        started = false;
+                    } else {
                     const float4 sp = A.src_pos[src];
                     xs = make_float3(sp.x, sp.y, sp.z);
                     srcleaf = A.src_leaf[src];
@@ -301,10 +352,13 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                     first = true;
                     ncross = 0;
                     ++c_rays;
+                    }  // not a hole
                 }
             }
         }
-        if (!__any_sync(kFull, active)) break;
+        // done only when the wave's queue is exhausted: a refill can hand out
+        // nothing but holes (unused chunk slots) while rays remain
+        if (!__any_sync(kFull, active) && exhausted) break;
 
         // ------------------------------- HG normalisation of new rays (shared)
         if (MODE != MODE_LL) {
@@ -469,7 +523,11 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
         // ------------------------------------------ high / low list appends
         {
             const bool wh = active && outcome == 2;
-            const unsigned long long slot = warp_append(wh, &wc->n_high, lane);
+            unsigned long long hb;
+            unsigned hn;
+            const unsigned long long slot = chunk_append(wh, &wc->n_high, &chunks[0], 64u, lane, &hb, &hn);
+            if (lane < static_cast<int>(hn) && hb + lane < static_cast<unsigned long long>(A.cap))
+                A.Hb[1 - par][hb + lane].src = -1;
             if (wh) {
                 if (slot < static_cast<unsigned long long>(A.cap)) {
                     RayRec r;
@@ -483,7 +541,9 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                 }
             }
             const bool wl = active && outcome == 3;
-            const unsigned long long slot2 = warp_append(wl, &wc->n_low, lane);
+            const unsigned long long slot2 = chunk_append(wl, &wc->n_low, &chunks[1], 32u, lane, &hb, &hn);
+            if (lane < static_cast<int>(hn) && hb + lane < static_cast<unsigned long long>(A.cap))
+                A.L_out[hb + lane].src = -1;
             if (wl) {
                 if (slot2 < static_cast<unsigned long long>(A.cap)) {
                     RayRec r;
@@ -508,7 +568,11 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
             for (int l = 0; l < NL; ++l) has = has || (sca[l] > 0.f);
             has = has && active && outcome == 0;
             bool direct_dep = false;
-            const unsigned long long rs = A.rec_cap > 0 ? warp_append(has, A.rec_n, lane) : 0ull;
+            unsigned long long rb = 0;
+            unsigned rn = 0;
+            const unsigned long long rs = A.rec_cap > 0 ? chunk_append(has, A.rec_n, &chunks[2], 256u, lane, &rb, &rn) : 0ull;
+            for (unsigned h = lane; h < rn; h += kWarp)
+                if (rb + h < static_cast<unsigned long long>(A.rec_cap)) A.rec_cell[rb + h] = 0xffffffffu;
             if (has && A.rec_cap == 0) {
                 direct_dep = true;
             } else if (has) {
@@ -600,6 +664,17 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
     }
 
     // ---------------------------------------------------------- flush
+    // unused slots of this warp's chunks are holes for the lists' readers
+    {
+        const ChunkState c0 = chunks[0], c1 = chunks[1], c2 = chunks[2];
+        for (unsigned h = lane; h < c0.left; h += kWarp)
+            if (c0.base + h < static_cast<unsigned long long>(A.cap)) A.Hb[1 - par][c0.base + h].src = -1;
+        for (unsigned h = lane; h < c1.left; h += kWarp)
+            if (c1.base + h < static_cast<unsigned long long>(A.cap)) A.L_out[c1.base + h].src = -1;
+        if (MODE != MODE_LL)
+            for (unsigned h = lane; h < c2.left; h += kWarp)
+                if (c2.base + h < static_cast<unsigned long long>(A.rec_cap)) A.rec_cell[c2.base + h] = 0xffffffffu;
+    }
     led.flush(sh_led, lane);
     atomicAdd(&sh_cnt[CT_RAYS], static_cast<unsigned long long>(c_rays));
     atomicAdd(&sh_cnt[CT_CROSS], static_cast<unsigned long long>(c_cross));
@@ -682,6 +757,7 @@ __global__ void merge_insert_kernel(const MergeArgs A) {
     const long long n_low = hc > 0 ? static_cast<long long>(min(pd->wc.n_low, static_cast<unsigned long long>(A.cap))) : 0;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n_low;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (A.L[i].src < 0) continue;  // hole of a warp's chunk
         const unsigned long long key = merge_key(A.L[i]);
         unsigned long long h = hash64(key) & static_cast<unsigned long long>(hc - 1);
         bool placed = false;
@@ -1014,8 +1090,8 @@ __global__ void rec_scatter_kernel(const PipeDev *pd, const unsigned long long *
     const long long warp0 = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) - lane;
     for (long long w = warp0; w < n; w += stride) {
         const long long i = w + lane;
-        const bool ok = i < n;
-        const unsigned c = ok ? cell[i] : 0xffffffffu;
+        const unsigned c = i < n ? cell[i] : 0xffffffffu;
+        const bool ok = c != 0xffffffffu;  // beyond the records, or a hole
         const unsigned peers = __match_any_sync(kFull, c);
         const int leader = __ffs(peers) - 1;
         unsigned base = 0;
@@ -1134,14 +1210,14 @@ __device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, 
 
 template <int PPL>
 __global__ void __launch_bounds__(kBlock) cell_accumulate_kernel(const DevGrid G, int l, const PipeDev *pd,
-                                                                 const unsigned long long *rec_n,
+                                                                 const int *n_sorted,
                                                                  const unsigned *scell, const float4 *sdir,
                                                                  const float *scoef, long long cap, float *pend) {
     __shared__ ulonglong2 sh_rec[kBlock / kWarp][kWarp];
     __shared__ ulonglong2 sh_rec2[kBlock / kWarp][kWarp];
     __shared__ unsigned sh_cell[kBlock / kWarp][kWarp];
     if (!pd->flush) return;
-    const long long n = static_cast<long long>(min(*rec_n, static_cast<unsigned long long>(cap)));
+    const long long n = static_cast<long long>(*n_sorted);  // records bucketed (holes excluded)
     const int lane = threadIdx.x & 31;
     const long long warps = static_cast<long long>(gridDim.x) * (blockDim.x / kWarp);
     const long long nranges = (n + kAccRange - 1) / kAccRange;
