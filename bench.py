@@ -177,6 +177,10 @@ def main():
     ap.add_argument("--src-stride", type=int, default=1,
                     help="profiling aid: trace every n-th primary source only (default: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # capacities (0 = automatic); results do not depend on them.  Smaller
+    # buffers keep the device footprint of a profiling run to a few GB.
+    ap.add_argument("--queue-rays", type=int, default=0)
+    ap.add_argument("--deposit-records", type=int, default=0)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -185,6 +189,10 @@ def main():
     grid, params = make_workload()
     if args.src_stride > 1:
         params = dict(params, src_stride=args.src_stride, src_offset=1)
+    if args.queue_rays:
+        params = dict(params, queue_rays=args.queue_rays)
+    if args.deposit_records:
+        params = dict(params, deposit_records=args.deposit_records)
     metric = "ray-cell crossings/s"
     unit = "crossings/s"
     config = {"workload": WORKLOAD, "n_leaf": grid.n_leaf, "a_rt": params["a_rt"], "f_l": F_L,
@@ -192,6 +200,8 @@ def main():
               "warmup_note": "the first warm-up step is the end-to-end run through host buffers"}
     if args.src_stride > 1:
         config["profiling_subset"] = f"every {args.src_stride}th primary source (not a bench value)"
+    if args.queue_rays or args.deposit_records:
+        config["capacities"] = {"queue_rays": args.queue_rays, "deposit_records": args.deposit_records}
 
     if args.impl == "reference":
         if rank != 0:
