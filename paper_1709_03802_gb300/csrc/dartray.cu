@@ -82,7 +82,7 @@ struct Pipe {
     int *d_hcnt = nullptr;
     int4 *d_hmem = nullptr;
     // deferred deposit records
-    unsigned *d_rec_cell = nullptr, *d_srt_cell = nullptr, *d_cnt = nullptr, *d_off = nullptr, *d_cur = nullptr;
+    unsigned *d_rec_cell = nullptr, *d_cnt = nullptr, *d_off = nullptr, *d_cur = nullptr;
     float4 *d_rec_dir = nullptr, *d_srt_dir = nullptr;
     float *d_rec_coef = nullptr, *d_srt_coef = nullptr;
     unsigned long long *d_rec_n = nullptr;
@@ -145,7 +145,7 @@ void free_all(dartray_grid *g) {
     for (int i = 0; i < kPipes; ++i) {
         Pipe &P = g->pipe[i];
         void *pp[] = {P.d_pd, P.d_H[0], P.d_H[1], P.d_M[0], P.d_M[1], P.d_L, P.d_HI[0], P.d_HI[1], P.d_MI[0],
-                      P.d_MI[1], P.d_LI, P.d_hkey, P.d_hcnt, P.d_hmem, P.d_rec_cell, P.d_srt_cell, P.d_cnt,
+                      P.d_MI[1], P.d_LI, P.d_hkey, P.d_hcnt, P.d_hmem, P.d_rec_cell, P.d_cnt,
                       P.d_off, P.d_cur, P.d_rec_dir, P.d_srt_dir, P.d_rec_coef, P.d_srt_coef, P.d_rec_n,
                       P.d_blocksum, P.d_total};
         for (void *p : pp)
@@ -247,14 +247,19 @@ int enqueue_flush(dartray_grid *g, Pipe &P, float *pend_dst, int force) {
     scan_offsets_kernel<<<1, 1, 0, s>>>(P.d_pd, P.d_blocksum, nb, P.d_total);
     scan_apply_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, P.d_cnt, g->n_leaf, P.d_blocksum, P.d_off, P.d_cur);
     rec_scatter_kernel<<<gb, kBlock, 0, s>>>(P.d_pd, P.d_rec_n, P.d_rec_cell, P.d_rec_dir, P.d_rec_coef, g->rec_cap,
-                                             g->nl, P.d_cur, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef);
+                                             g->nl, P.d_cur, P.d_srt_dir, P.d_srt_coef);
+    const int packed = g->nl == 1;
     for (int l = 0; l < g->nl; ++l) {
+#define ACC(PPL) \
+    cell_accumulate_kernel<PPL><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_total, P.d_off, g->n_leaf, P.d_srt_dir, \
+                                                      P.d_srt_coef, g->rec_cap, packed, pend_dst)
         switch (g->k_lam[l]) {
-        case 0: cell_accumulate_kernel<1><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_total, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
-        case 1: cell_accumulate_kernel<2><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_total, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
-        case 2: cell_accumulate_kernel<6><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_total, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
-        default: cell_accumulate_kernel<24><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_total, P.d_srt_cell, P.d_srt_dir, P.d_srt_coef, g->rec_cap, pend_dst); break;
+        case 0: ACC(1); break;
+        case 1: ACC(2); break;
+        case 2: ACC(6); break;
+        default: ACC(24); break;
         }
+#undef ACC
     }
     flush_reset_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, P.d_rec_n, P.d_cnt, g->n_leaf);
     g->launches += 6 + g->nl;
@@ -775,11 +780,12 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
         AL(P.d_pd, 1);
         if (g->rec_cap > 0) {
             AL(P.d_rec_cell, g->rec_cap);
-            AL(P.d_srt_cell, g->rec_cap);
             AL(P.d_rec_dir, g->rec_cap);
             AL(P.d_srt_dir, g->rec_cap);
-            AL(P.d_rec_coef, static_cast<size_t>(g->rec_cap) * nl);
-            AL(P.d_srt_coef, static_cast<size_t>(g->rec_cap) * nl);
+            if (nl > 1) {  // one wavelength: the coefficient is stored in the direction's w
+                AL(P.d_rec_coef, static_cast<size_t>(g->rec_cap) * nl);
+                AL(P.d_srt_coef, static_cast<size_t>(g->rec_cap) * nl);
+            }
             AL(P.d_cnt, desc->n_leaf);
             AL(P.d_off, desc->n_leaf);
             AL(P.d_cur, desc->n_leaf);

@@ -288,6 +288,17 @@ __device__ inline int next_leaf(const DevGrid &G, int leaf, int tie, const float
     return follow_link(G, code, a, __ldg(&G.leaf_box[leaf]), pe, n, &b, &hb);
 }
 
+// Reciprocal square root of the Henyey-Greenstein weights (Eq. 4): the
+// hardware approximation with denormals flushed.  Its arguments,
+// 1 + g^2 - 2g cos(theta), are at least (1 - |g|)^2, far from the denormal
+// range.  The row sums Z and the row expansion both use it, so each deposited
+// row is normalised with the weights it is expanded with.
+__device__ __forceinline__ float hg_rsqrt(float t) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
+    return r;
+}
+
 // ------------------------------------------------------------------ rays
 enum RayKind : int { kSeed = 0, kChild = 1, kMerged = 2, kResumed = 3 };
 

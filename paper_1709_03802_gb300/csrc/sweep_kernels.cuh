@@ -42,8 +42,8 @@ struct MarchArgs {
     // deferred j_sca deposit: one record per depositing crossing (cell, ray
     // direction, scattered luminosity / HG row sum per wavelength)
     unsigned *rec_cell;
-    float4 *rec_dir;
-    float *rec_coef;              // [nl][rec_cap]
+    float4 *rec_dir;              // direction; w = coefficient when nl == 1
+    float *rec_coef;              // [nl][rec_cap] (nl > 1 only)
     unsigned long long *rec_n;
     unsigned *rec_cnt;            // records per cell (for the bucketing)
     long long rec_cap;
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                     float part = 0.f;
                     for (int q = lane; q < npx[l]; q += kWarp) {
                         const float4 pd = sh_pix[pixbase[l] + q];
-                        const float r = rsqrtf(hgB[l] - hgC[l] * (pd.x * nx + pd.y * ny + pd.z * nz));
+                        const float r = hg_rsqrt(hgB[l] - hgC[l] * (pd.x * nx + pd.y * ny + pd.z * nz));
                         part += r * r * r;
                     }
 #pragma unroll
@@ -579,10 +579,11 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                 if (rs < static_cast<unsigned long long>(A.rec_cap)) {
                     atomicAdd(&A.rec_cnt[leaf], 1u);
                     A.rec_cell[rs] = static_cast<unsigned>(leaf);
-                    A.rec_dir[rs] = make_float4(n.x, n.y, n.z, 0.f);
+                    // one wavelength: the coefficient rides in the direction's w
+                    A.rec_dir[rs] = make_float4(n.x, n.y, n.z, NL == 1 ? sca[0] : 0.f);
 #pragma unroll
                     for (int l = 0; l < NL; ++l) {
-                        A.rec_coef[l * A.rec_cap + static_cast<long long>(rs)] = sca[l];
+                        if (NL > 1) A.rec_coef[l * A.rec_cap + static_cast<long long>(rs)] = sca[l];
                         if (sca[l] != 0.f) c_jpix += static_cast<unsigned>(npx[l]);
                     }
                 } else {
@@ -604,7 +605,7 @@ __global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march
                     float *row = A.pend_dst + G.off_lam[l] + static_cast<long long>(lj) * npx[l];
                     for (int q = lane; q < npx[l]; q += kWarp) {
                         const float4 pd = sh_pix[pixbase[l] + q];
-                        const float r = rsqrtf(hgB[l] - hgC[l] * (pd.x * nx + pd.y * ny + pd.z * nz));
+                        const float r = hg_rsqrt(hgB[l] - hgC[l] * (pd.x * nx + pd.y * ny + pd.z * nz));
                         atomicAdd(row + q, coef * (r * r * r));
                     }
                 }
@@ -998,7 +999,7 @@ __global__ void ztab_kernel(const DevGrid G, float *ztab, long long ndt) {
         float z = 0.f;
         for (int q = 0; q < np; ++q) {
             const float4 v = pd[q];
-            const float r = rsqrtf(B - Cg * (v.x * n.x + v.y * n.y + v.z * n.z));
+            const float r = hg_rsqrt(B - Cg * (v.x * n.x + v.y * n.y + v.z * n.z));
             z += r * r * r;
         }
         ztab[l * ndt + i] = z;
@@ -1075,33 +1076,48 @@ __global__ void flush_reset_kernel(PipeDev *pd, unsigned long long *rec_n, unsig
     if (blockIdx.x == 0 && threadIdx.x == 0) *rec_n = 0;
 }
 
-// Bucket records by cell.  Consecutive records often share a cell (they come
-// from one warp of the marcher), so the lanes of a warp that hold the same
-// cell take their cursor positions with one atomic.
+// Bucket records by cell (counting sort; the cursors start at the cells'
+// offsets).  Consecutive records often share a cell (they come from one warp
+// of the marcher), so the lanes of a warp that hold the same cell take their
+// positions with one atomic.  A warp handles kScatterUnroll groups of 32
+// records at once so that their cursor atomics are in flight together.
+constexpr int kScatterUnroll = 4;
 __global__ void rec_scatter_kernel(const PipeDev *pd, const unsigned long long *rec_n, const unsigned *cell,
                                    const float4 *dir, const float *coef, long long cap, int nl, unsigned *cur,
-                                   unsigned *scell, float4 *sdir, float *scoef) {
+                                   float4 *sdir, float *scoef) {
     if (!pd->flush) return;
     const long long n = static_cast<long long>(min(*rec_n, static_cast<unsigned long long>(cap)));
-    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
     const int lane = threadIdx.x & 31;
-    // every lane of a warp runs the same number of iterations (warp-uniform
-    // bound) so the warp-wide match below is always converged
-    const long long warp0 = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) - lane;
-    for (long long w = warp0; w < n; w += stride) {
-        const long long i = w + lane;
-        const unsigned c = i < n ? cell[i] : 0xffffffffu;
-        const bool ok = c != 0xffffffffu;  // beyond the records, or a hole
-        const unsigned peers = __match_any_sync(kFull, c);
-        const int leader = __ffs(peers) - 1;
-        unsigned base = 0;
-        if (ok && lane == leader) base = atomicAdd(&cur[c], static_cast<unsigned>(__popc(peers)));
-        base = __shfl_sync(kFull, base, leader);
-        if (ok) {
-            const unsigned pos = base + __popc(peers & ((1u << lane) - 1u));
-            scell[pos] = c;
-            sdir[pos] = dir[i];
-            for (int l = 0; l < nl; ++l) scoef[l * cap + pos] = coef[l * cap + i];
+    const unsigned below = (1u << lane) - 1u;
+    const long long warp = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+    const long long per = static_cast<long long>(kWarp) * kScatterUnroll;
+    const long long stride = ((static_cast<long long>(gridDim.x) * blockDim.x) >> 5) * per;
+    // warp-uniform trip count: the warp-wide match below is always converged
+    for (long long base = warp * per; base < n; base += stride) {
+        unsigned c[kScatterUnroll], peers[kScatterUnroll], pos[kScatterUnroll];
+        float4 dv[kScatterUnroll];
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            const long long i = base + u * kWarp + lane;
+            c[u] = i < n ? cell[i] : 0xffffffffu;  // beyond the records, or a hole
+            dv[u] = i < n ? dir[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            peers[u] = __match_any_sync(kFull, c[u]);
+            pos[u] = 0;
+            if (c[u] != 0xffffffffu && lane == __ffs(peers[u]) - 1)
+                pos[u] = atomicAdd(&cur[c[u]], static_cast<unsigned>(__popc(peers[u])));
+        }
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            const unsigned p = __shfl_sync(kFull, pos[u], __ffs(peers[u]) - 1) + __popc(peers[u] & below);
+            if (c[u] != 0xffffffffu) {
+                const long long i = base + u * kWarp + lane;
+                sdir[p] = dv[u];
+                if (nl > 1)
+                    for (int l = 0; l < nl; ++l) scoef[l * cap + p] = coef[l * cap + i];
+            }
         }
     }
 }
@@ -1131,14 +1147,44 @@ __device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsig
     return d;
 }
 
-// Accumulate the records [beg, end) (sorted by cell) of wavelength l into the
-// pending rows; a row is flushed (with atomics: neighbouring ranges may share
-// the cell) whenever the cell changes.  Each lane owns PPL pixels, evaluated
-// in pairs: t = 1 + g^2 - 2g n_q.n, w = t^(-3/2), acc += coef w.
+// The cell holding sorted record p: the last c with off[c] <= p (off is the
+// exclusive prefix sum of the per-cell record counts).  32-way search, all
+// lanes of the warp together.
+__device__ inline int cell_of_record(const unsigned *off, int n_leaf, long long p, int lane) {
+    int lo = 0, hi = n_leaf;  // off[lo] <= p; the answer lies in [lo, hi)
+    while (hi - lo > 1) {
+        const int step = (hi - lo + kWarp - 1) / kWarp;
+        const long long c = lo + static_cast<long long>(lane + 1) * step;
+        const bool le = c < hi && off[c] <= p;  // true on a prefix of the lanes
+        const int k = __popc(__ballot_sync(kFull, le));
+        lo += k * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
+
+// From cell cur (whose records end at or before p) to the cell holding record
+// p: the cells after cur are scanned 32 at a time.
+__device__ inline int advance_cell(const unsigned *off, int n_leaf, int cur, long long p, int lane) {
+    for (;;) {
+        const long long c = static_cast<long long>(cur) + 1 + lane;
+        const bool le = c < n_leaf && off[c] <= p;
+        const int k = __popc(__ballot_sync(kFull, le));
+        cur += k;
+        if (k < kWarp) return cur;
+    }
+}
+
+// Accumulate the sorted records [beg, end) of wavelength l into the pending
+// rows; a row is flushed (with atomics: neighbouring ranges may share the
+// cell) whenever the cell changes, the cell boundaries coming from the
+// offsets.  Each lane owns PPL pixels, evaluated in pairs:
+// t = 1 + g^2 - 2g n_q.n, w = t^(-3/2), acc += coef w.
 template <int PPL>
-__device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, long long end, const unsigned *scell,
-                                        const float4 *sdir, const float *scoef, long long cap, float *pend,
-                                        int lane, ulonglong2 *sh_rec, ulonglong2 *sh_rec2, unsigned *sh_cell) {
+__device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, long long end, long long total,
+                                        const unsigned *off, int n_leaf, const float4 *sdir, const float *scoef,
+                                        long long cap, bool packed, float *pend, int lane, ulonglong2 *sh_rec,
+                                        ulonglong2 *sh_rec2) {
     constexpr int NP2 = (PPL + 1) / 2;
     const int k = G.k_lam[l];
     const int np = 12 << (2 * k);
@@ -1159,8 +1205,9 @@ __device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, 
         acc[i] = f2_pack(make_float2(0.f, 0.f));
     }
     const unsigned long long B2 = f2_pack(make_float2(B, B));
-    unsigned cur = scell[beg];
-    auto flush = [&](unsigned c) {
+    int cur = cell_of_record(off, n_leaf, beg, lane);
+    long long nb = cur + 1 < n_leaf ? static_cast<long long>(off[cur + 1]) : total;  // end of cur's records
+    auto flush = [&](int c) {
         float *row = pend + G.off_lam[l] + static_cast<long long>(c) * np;
 #pragma unroll
         for (int i = 0; i < NP2; ++i) {
@@ -1177,21 +1224,20 @@ __device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, 
             // staged as duplicated pairs (x, x) so the loop below reads
             // ready-made f32x2 operands
             const float4 dv = sdir[r];
-            const float cf = scoef[l * cap + r];
+            const float cf = packed ? dv.w : scoef[l * cap + r];
             sh_rec[lane] = make_ulonglong2(f2_pack(make_float2(Cg * dv.x, Cg * dv.x)),
                                            f2_pack(make_float2(Cg * dv.y, Cg * dv.y)));
             sh_rec2[lane] = make_ulonglong2(f2_pack(make_float2(Cg * dv.z, Cg * dv.z)), f2_pack(make_float2(cf, cf)));
-            sh_cell[lane] = scell[r];
         }
         __syncwarp();
         const int cntj = static_cast<int>(min(static_cast<long long>(kWarp), end - b));
         for (int j = 0; j < cntj; ++j) {
-            const ulonglong2 ra = sh_rec[j], rb = sh_rec2[j];
-            const unsigned cj = sh_cell[j];
-            if (cj != cur) {
+            if (b + j >= nb) {  // warp-uniform: the next cell's records begin
                 flush(cur);
-                cur = cj;
+                cur = advance_cell(off, n_leaf, cur, b + j, lane);
+                nb = cur + 1 < n_leaf ? static_cast<long long>(off[cur + 1]) : total;
             }
+            const ulonglong2 ra = sh_rec[j], rb = sh_rec2[j];
             const unsigned long long cx = ra.x, cy = ra.y, cz = rb.x, cc = rb.y;
 #pragma unroll
             for (int i = 0; i < NP2; ++i) {
@@ -1199,7 +1245,7 @@ __device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, 
                 t = f2_fma(my[i], cy, t);
                 t = f2_fma(mz[i], cz, t);
                 const float2 tv = f2_unpack(t);
-                const unsigned long long rr = f2_pack(make_float2(rsqrtf(tv.x), rsqrtf(tv.y)));
+                const unsigned long long rr = f2_pack(make_float2(hg_rsqrt(tv.x), hg_rsqrt(tv.y)));
                 acc[i] = f2_fma(cc, f2_mul(f2_mul(rr, rr), rr), acc[i]);
             }
         }
@@ -1210,22 +1256,22 @@ __device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, 
 
 template <int PPL>
 __global__ void __launch_bounds__(kBlock) cell_accumulate_kernel(const DevGrid G, int l, const PipeDev *pd,
-                                                                 const int *n_sorted,
-                                                                 const unsigned *scell, const float4 *sdir,
-                                                                 const float *scoef, long long cap, float *pend) {
+                                                                 const int *n_sorted, const unsigned *off,
+                                                                 int n_leaf, const float4 *sdir,
+                                                                 const float *scoef, long long cap, int packed,
+                                                                 float *pend) {
     __shared__ ulonglong2 sh_rec[kBlock / kWarp][kWarp];
     __shared__ ulonglong2 sh_rec2[kBlock / kWarp][kWarp];
-    __shared__ unsigned sh_cell[kBlock / kWarp][kWarp];
     if (!pd->flush) return;
     const long long n = static_cast<long long>(*n_sorted);  // records bucketed (holes excluded)
-    const int lane = threadIdx.x & 31;
     const long long warps = static_cast<long long>(gridDim.x) * (blockDim.x / kWarp);
     const long long nranges = (n + kAccRange - 1) / kAccRange;
+    const int lane = threadIdx.x & 31;
     for (long long w = blockIdx.x * static_cast<long long>(blockDim.x / kWarp) + (threadIdx.x >> 5); w < nranges;
          w += warps) {
         const long long beg = w * kAccRange, end = min(n, beg + kAccRange);
-        accumulate_range<PPL>(G, l, beg, end, scell, sdir, scoef, cap, pend, lane, sh_rec[threadIdx.x >> 5],
-                              sh_rec2[threadIdx.x >> 5], sh_cell[threadIdx.x >> 5]);
+        accumulate_range<PPL>(G, l, beg, end, n, off, n_leaf, sdir, scoef, cap, packed != 0, pend, lane,
+                              sh_rec[threadIdx.x >> 5], sh_rec2[threadIdx.x >> 5]);
     }
 }
 
