@@ -134,9 +134,15 @@ typedef struct dartray_stats {
     double l_sca2;        /* total scattered luminosity at the end of step 2 */
     double gpu_ms;        /* device time of the call (CUDA events) */
     int64_t kernel_launches; /* kernels launched by the call */
-    double march_ms;      /* with params.profile: summed ray-march kernel time */
+    double march_ms;      /* with params.profile: time covered by ray-march kernels */
     int64_t march_launches; /* ray-march kernel launches of the call */
     int64_t jsca_pixels;  /* scattering source-function pixels updated */
+    double flush_ms;      /* with params.profile: time covered by the deposit flushes
+                             (record bucketing and per-cell expansion) */
+    double busy_ms;       /* with params.profile: time covered by whole waves (march,
+                             low-list merge, flush, wave advance) of either pipeline */
+    int64_t restarts;     /* phase restarts with smaller source batches after a ray-queue
+                             overflow (the result does not depend on them) */
 } dartray_stats;
 
 /* Fill *p with the defaults above (r_pre is set when the grid is created if

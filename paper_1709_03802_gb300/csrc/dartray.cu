@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <utility>
 #include <cmath>
 #include <cstdio>
@@ -129,8 +130,11 @@ struct dartray_grid {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long rec_cap = 0;
     cudaEvent_t mev0 = nullptr, mev1 = nullptr;  // around each march launch (profile mode)
-    double march_ms = 0.0;
-    long long march_launches = 0;
+    double march_ms = 0.0, flush_ms = 0.0, busy_ms = 0.0;
+    long long march_launches = 0, restarts = 0;
+    // peak rays per source of each mode's waves, learned by earlier calls: the
+    // first batch of a phase is sized with it (0: not yet known)
+    double rays_per_src[3] = {0.0, 0.0, 0.0};
 };
 
 namespace {
@@ -237,7 +241,7 @@ int build_sources(dartray_grid *g, int mode, const float *pend_src, int *n_src) 
 // records into the pending j_sca rows (bucket by cell, then per-cell-range
 // accumulation).  On the device the kernels run only when the buffer is at
 // least half full, or always when force is set.
-int enqueue_flush(dartray_grid *g, Pipe &P, float *pend_dst, int force) {
+int enqueue_flush_kernels(dartray_grid *g, Pipe &P, float *pend_dst, int force) {
     if (g->rec_cap == 0) return DARTRAY_OK;
     cudaStream_t s = P.stream;
     const int nb = (g->n_leaf + kBlock - 1) / kBlock;
@@ -267,7 +271,7 @@ int enqueue_flush(dartray_grid *g, Pipe &P, float *pend_dst, int force) {
     return DARTRAY_OK;
 }
 
-struct MarchTiming {
+struct SpanTiming {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[kPipes];
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<float, float>> spans;  // [start, end] ms after the phase origin
@@ -311,17 +315,57 @@ struct MarchTiming {
         if (ce > cs) tot += ce - cs;
         return tot;
     }
-    ~MarchTiming() {
+    ~SpanTiming() {
         for (auto &v : pending)
             for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
         for (auto e : pool) cudaEventDestroy(e);
     }
 };
 
+// Device-event spans of one phase (params.profile): march kernels, deposit
+// flushes and whole waves; each is reported as the length of its union.
+struct PhaseTiming {
+    SpanTiming march, flush, wave;
+    cudaEvent_t origin = nullptr;
+    ~PhaseTiming() {
+        if (origin) cudaEventDestroy(origin);
+    }
+    void start(cudaStream_t s) {
+        cudaEventCreate(&origin);
+        cudaEventRecord(origin, s);
+        cudaEventSynchronize(origin);
+        march.origin = flush.origin = wave.origin = origin;
+    }
+    void collect(int i) {
+        march.collect(i);
+        flush.collect(i);
+        wave.collect(i);
+    }
+};
+
+// records a device-event span around the work enqueued by f on stream s
+template <class F>
+int timed(SpanTiming *t, int pi, cudaStream_t s, F &&f) {
+    if (!t) return f();
+    cudaEvent_t e0 = t->get(), e1 = t->get();
+    CK(cudaEventRecord(e0, s));
+    const int rc = f();
+    if (rc) return rc;
+    CK(cudaEventRecord(e1, s));
+    t->pending[pi].emplace_back(e0, e1);
+    return DARTRAY_OK;
+}
+
+int enqueue_flush(dartray_grid *g, Pipe &P, float *pend_dst, int force, PhaseTiming *pt, int pi) {
+    if (g->rec_cap == 0) return DARTRAY_OK;
+    return timed(pt ? &pt->flush : nullptr, pi, P.stream,
+                 [&] { return enqueue_flush_kernels(g, P, pend_dst, force); });
+}
+
 // Enqueue one wave of pipeline P: march, merge the low list, flush records
 // when the buffer is half full, advance to the next wave.
-int enqueue_wave(dartray_grid *g, Pipe &P, int pi, int mode, const MarchArgs &base, float *pend_dst,
-                 MarchTiming *tm) {
+int enqueue_wave_kernels(dartray_grid *g, Pipe &P, int pi, int mode, const MarchArgs &base, float *pend_dst,
+                         PhaseTiming *pt) {
     cudaStream_t s = P.stream;
     MarchArgs A = base;
     A.pd = P.d_pd;
@@ -338,18 +382,8 @@ int enqueue_wave(dartray_grid *g, Pipe &P, int pi, int mode, const MarchArgs &ba
     A.rec_coef = P.d_rec_coef;
     A.rec_n = P.d_rec_n;
     A.rec_cnt = P.d_cnt;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (tm) {
-        e0 = tm->get();
-        e1 = tm->get();
-        CK(cudaEventRecord(e0, s));
-    }
-    int rc = launch_march(g, s, mode, A);
+    int rc = timed(pt ? &pt->march : nullptr, pi, s, [&] { return launch_march(g, s, mode, A); });
     if (rc) return rc;
-    if (tm) {
-        CK(cudaEventRecord(e1, s));
-        tm->pending[pi].emplace_back(e0, e1);
-    }
     ++g->march_launches;
     MergeArgs M{};
     M.pd = P.d_pd;
@@ -373,13 +407,19 @@ int enqueue_wave(dartray_grid *g, Pipe &P, int pi, int mode, const MarchArgs &ba
     merge_emit_kernel<<<mg, kBlock, 0, s>>>(M);
     g->launches += 4;
     if (mode != MODE_LL) {
-        rc = enqueue_flush(g, P, pend_dst, 0);
+        rc = enqueue_flush(g, P, pend_dst, 0, pt, pi);
         if (rc) return rc;
     }
     wave_advance_kernel<<<1, 1, 0, s>>>(P.d_pd);
     ++g->launches;
     CK(cudaGetLastError());
     return DARTRAY_OK;
+}
+
+int enqueue_wave(dartray_grid *g, Pipe &P, int pi, int mode, const MarchArgs &base, float *pend_dst,
+                 PhaseTiming *pt) {
+    return timed(pt ? &pt->wave : nullptr, pi, P.stream,
+                 [&] { return enqueue_wave_kernels(g, P, pi, mode, base, pend_dst, pt); });
 }
 
 int start_batch(dartray_grid *g, Pipe &P, int src_lo, int nb, int kstart) {
@@ -468,12 +508,17 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
     // Sources are traced in batches (the phase is additive over sources and
     // U_LL is fixed during a phase, so batching does not change the result),
     // two batches at a time on two streams so that one batch's last waves
-    // overlap the other's.  The batch size follows the peak rays per source
-    // of a wave seen so far; an overflow restarts the phase with smaller
-    // batches.
+    // overlap the other's.  A batch is sized so that its largest wave fills
+    // 80% of a queue, from an estimate of the peak rays per source.  The
+    // estimate starts high (small first batches), halves after each batch but
+    // never drops below the heaviest batch seen, in this call or an earlier
+    // one of the same step; an overflow restarts the phase with smaller
+    // batches, so it is worth avoiding.
     const long long npix0 = 12ll << (2 * kstart);
     long long batch_cap = g->P.src_batch > 0 ? g->P.src_batch : n_src;
-    double rays_per_src = static_cast<double>(npix0) * 16.0;
+    const double rps_floor = g->rays_per_src[mode];
+    double rays_per_src = rps_floor > 0.0 ? rps_floor
+                                          : std::max(static_cast<double>(npix0) * 16.0, g->cap / 64.0);
     constexpr int kWavesAhead = 6;
     DevStats snap{};
     CK(cudaMemcpyAsync(&snap, g->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
@@ -503,21 +548,28 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
         std::memset(fresh.ledger, 0, sizeof fresh.ledger);
         CK(cudaMemcpyAsync(g->d_st, &fresh, sizeof(DevStats), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));  // the pipelines start after the setup
-        std::unique_ptr<MarchTiming> tm;
+        std::unique_ptr<PhaseTiming> tm;
         if (g->P.profile) {
-            tm.reset(new MarchTiming());
-            CK(cudaEventCreate(&tm->origin));
-            CK(cudaEventRecord(tm->origin, s));
-            CK(cudaEventSynchronize(tm->origin));
+            tm.reset(new PhaseTiming());
+            tm->start(s);
         }
         long long waves = 0;
+        double max_rps = 0.0;  // largest peak wave per source of a batch
         bool overflow = false;
         long long failed_nb = 0;
         long long next = 0;
+        // Each pipeline runs kWavesAhead waves per host round trip.  The host
+        // refills whichever pipeline finishes its waves first, so neither
+        // waits for the other.
+        bool inflight[kPipes] = {};
         for (;;) {
             bool any = false;
             for (int i = 0; i < kPipes; ++i) {
                 Pipe &P = g->pipe[i];
+                if (inflight[i]) {
+                    any = true;
+                    continue;
+                }
                 if (!P.active && next < n_src) {
                     long long want = static_cast<long long>(0.8 * static_cast<double>(g->cap) / rays_per_src);
                     want = std::max<long long>(1, std::min(want, batch_cap));
@@ -531,26 +583,39 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
                         if ((rc = enqueue_wave(g, P, i, mode, base, pend_dst, tm.get()))) return rc;
                     CK(cudaMemcpyAsync(P.h_pd, P.d_pd, sizeof(PipeDev), cudaMemcpyDeviceToHost, P.stream));
                     CK(cudaEventRecord(P.ev, P.stream));
+                    inflight[i] = true;
                 }
             }
             if (!any) break;
-            for (int i = 0; i < kPipes; ++i) {
-                Pipe &P = g->pipe[i];
-                if (!P.active) continue;
-                CK(cudaEventSynchronize(P.ev));
-                if (tm) tm->collect(i);
-                const PipeDev &h = *P.h_pd;
-                if (h.wc.status & ST_QUEUE) {
-                    overflow = true;
-                    failed_nb = std::max<long long>(failed_nb, P.nb);
-                } else if ((rc = status_error(h, mode))) {
-                    return rc;
+            // the first pipeline whose waves have completed
+            int i = -1;
+            while (i < 0) {
+                for (int j = 0; j < kPipes && i < 0; ++j) {
+                    if (!inflight[j]) continue;
+                    const cudaError_t q = cudaEventQuery(g->pipe[j].ev);
+                    if (q == cudaSuccess) i = j;
+                    else if (q != cudaErrorNotReady) return fail(DARTRAY_E_CUDA, cudaGetErrorString(q));
                 }
-                if (h.done) {
-                    P.active = false;
-                    waves += h.waves;
-                    rays_per_src = std::max(rays_per_src * 0.5, static_cast<double>(h.peak) / P.nb);
-                }
+                if (i < 0) std::this_thread::yield();
+            }
+            Pipe &P = g->pipe[i];
+            inflight[i] = false;
+            if (tm) tm->collect(i);
+            const PipeDev &h = *P.h_pd;
+            if (h.wc.status & ST_QUEUE) {
+                overflow = true;
+                failed_nb = std::max<long long>(failed_nb, P.nb);
+            } else if ((rc = status_error(h, mode))) {
+                return rc;
+            }
+            if (h.done) {
+                P.active = false;
+                waves += h.waves;
+                const double r = static_cast<double>(h.peak) / P.nb;
+                max_rps = std::max(max_rps, r);
+                // never below the heaviest batch so far: an overflow restarts
+                // the whole phase
+                rays_per_src = std::max({rays_per_src * 0.5, max_rps, rps_floor});
             }
             if (overflow) break;
         }
@@ -558,10 +623,17 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
         if (!overflow) {
             // last records of both pipelines
             for (int i = 0; i < kPipes && mode != MODE_LL; ++i) {
-                if ((rc = enqueue_flush(g, g->pipe[i], pend_dst, 1))) return rc;
+                if ((rc = enqueue_flush(g, g->pipe[i], pend_dst, 1, tm.get(), i))) return rc;
                 CK(cudaStreamSynchronize(g->pipe[i].stream));
+                if (tm) tm->collect(i);
             }
-            if (tm) g->march_ms += tm->busy_ms();
+            if (tm) {
+                g->march_ms += tm->march.busy_ms();
+                g->flush_ms += tm->flush.busy_ms();
+                // the final flushes count as busy time too
+                for (auto &sp : tm->flush.spans) tm->wave.spans.push_back(sp);
+                g->busy_ms += tm->wave.busy_ms();
+            }
             DevStats out{};
             CK(cudaMemcpyAsync(&out, g->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
@@ -570,8 +642,10 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
             CK(cudaMemcpyAsync(g->d_st, &out, sizeof(DevStats), cudaMemcpyHostToDevice, s));
             std::memcpy(res->ledger, out.ledger, sizeof res->ledger);
             std::memcpy(res->cnt, out.cnt, sizeof res->cnt);
+            g->rays_per_src[mode] = std::max(rps_floor, max_rps);
             break;
         }
+        ++g->restarts;
         if (failed_nb <= 1) return fail(DARTRAY_E_QUEUE, "ray queues overflow with a single source");
         batch_cap = std::max<long long>(1, failed_nb / 4);
         rays_per_src = std::max(rays_per_src, 0.8 * static_cast<double>(g->cap) / batch_cap);
@@ -877,8 +951,8 @@ int dartray_direct(dartray_grid *g, dartray_stats *stats) {
     CK(cudaMemsetAsync(g->d_jtot, 0, g->sca_len * sizeof(float), g->stream));
     g->cur = 0;  // step 2 deposits into d_pend[1]
     const long long l0 = g->launches;
-    g->march_ms = 0.0;
-    g->march_launches = 0;
+    g->march_ms = g->flush_ms = g->busy_ms = 0.0;
+    g->march_launches = g->restarts = 0;
     CK(cudaEventRecord(g->ev0, g->stream));
     PhaseResult r1{}, r2{};
     if ((rc = run_phase(g, MODE_LL, &r1))) return rc;
@@ -895,6 +969,9 @@ int dartray_direct(dartray_grid *g, dartray_stats *stats) {
         stats->kernel_launches = g->launches - l0;
         stats->march_ms = g->march_ms;
         stats->march_launches = g->march_launches;
+        stats->flush_ms = g->flush_ms;
+        stats->busy_ms = g->busy_ms;
+        stats->restarts = g->restarts;
     }
     return DARTRAY_OK;
 }
@@ -907,8 +984,8 @@ int dartray_scatter_iter(dartray_grid *g, double *remaining_frac, dartray_stats 
     if (rc) return rc;
     CK(cudaMemsetAsync(g->d_st, 0, sizeof(DevStats), g->stream));
     const long long l0 = g->launches;
-    g->march_ms = 0.0;
-    g->march_launches = 0;
+    g->march_ms = g->flush_ms = g->busy_ms = 0.0;
+    g->march_launches = g->restarts = 0;
     CK(cudaEventRecord(g->ev0, g->stream));
     PhaseResult r{};
     if ((rc = run_phase(g, MODE_SCATTER, &r))) return rc;
@@ -923,6 +1000,9 @@ int dartray_scatter_iter(dartray_grid *g, double *remaining_frac, dartray_stats 
         stats->kernel_launches = g->launches - l0;
         stats->march_ms = g->march_ms;
         stats->march_launches = g->march_launches;
+        stats->flush_ms = g->flush_ms;
+        stats->busy_ms = g->busy_ms;
+        stats->restarts = g->restarts;
     }
     return DARTRAY_OK;
 }
