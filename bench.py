@@ -131,6 +131,7 @@ def run_step(gpu, grid):
     st = gpu.direct()
     cross = st["crossings"]
     march_ms = st["march_ms"]
+    flush_ms = st["flush_ms"]
     march_cross = st["crossings"]
     jpix = st["jsca_pixels"]
     launches = st["kernel_launches"]
@@ -141,6 +142,7 @@ def run_step(gpu, grid):
         it += 1
         cross += s2["crossings"]
         march_ms += s2["march_ms"]
+        flush_ms += s2["flush_ms"]
         march_cross += s2["crossings"]
         jpix += s2["jsca_pixels"]
         launches += s2["kernel_launches"]
@@ -149,7 +151,7 @@ def run_step(gpu, grid):
             break
     m = gpu.map(OBSERVER, MAP_K, max_sub=MAP_SUB, use_jsca=True)
     launches += 1
-    return dict(crossings=cross, march_ms=march_ms, march_crossings=march_cross, jsca_pixels=jpix,
+    return dict(crossings=cross, march_ms=march_ms, flush_ms=flush_ms, march_crossings=march_cross, jsca_pixels=jpix,
                 iters=it, iter_ms=it_ms, launches=launches, map=m)
 
 
@@ -298,7 +300,9 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
                 "kernel": "march_kernel (ray marcher)", "peak_source": peak_src,
-                "kernel_busy_share_of_step": march_ms / total_ms if total_ms else None}
+                "kernel_busy_share_of_step": march_ms / total_ms if total_ms else None,
+                "deposit_flush_share_of_step": (sum(r["flush_ms"] for r in results) / total_ms
+                                                if total_ms else None)}
     gpu.close()
 
     cpu = None
