@@ -291,8 +291,9 @@ __device__ inline int next_leaf(const DevGrid &G, int leaf, int tie, const float
 // Reciprocal square root of the Henyey-Greenstein weights (Eq. 4): the
 // hardware approximation with denormals flushed.  Its arguments,
 // 1 + g^2 - 2g cos(theta), are at least (1 - |g|)^2, far from the denormal
-// range.  The row sums Z and the row expansion both use it, so each deposited
-// row is normalised with the weights it is expanded with.
+// range.  The row sums Z and the row expansion both use it, so a row's
+// normalisation and its expansion differ only in the rounding order of the
+// dot product.
 __device__ __forceinline__ float hg_rsqrt(float t) {
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
