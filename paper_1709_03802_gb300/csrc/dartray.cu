@@ -127,6 +127,7 @@ struct dartray_grid {
     long long launches = 0;
     int num_sms = 1;
     int march_blocks = 1;
+    int acc_blocks[4] = {1, 1, 1, 1};  // resident blocks of cell_accumulate_kernel<1, 2, 6, 24>
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long rec_cap = 0;
     cudaEvent_t mev0 = nullptr, mev1 = nullptr;  // around each march launch (profile mode)
@@ -255,7 +256,7 @@ int enqueue_flush_kernels(dartray_grid *g, Pipe &P, float *pend_dst, int force) 
     const int packed = g->nl == 1;
     for (int l = 0; l < g->nl; ++l) {
 #define ACC(PPL) \
-    cell_accumulate_kernel<PPL><<<gb, kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_total, P.d_off, g->n_leaf, P.d_srt_dir, \
+    cell_accumulate_kernel<PPL><<<g->acc_blocks[PPL == 1 ? 0 : (PPL == 2 ? 1 : (PPL == 6 ? 2 : 3))], kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_total, P.d_off, g->n_leaf, P.d_srt_dir, \
                                                       P.d_srt_coef, g->rec_cap, packed, pend_dst)
         switch (g->k_lam[l]) {
         case 0: ACC(1); break;
@@ -924,6 +925,12 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
     }
     ztab_kernel<<<static_cast<unsigned>((ndir + kBlock - 1) / kBlock), kBlock, 0, s>>>(G, g->d_ztab, ndir);
     ++g->launches;
+    // the expansion kernel runs one block per resident slot (its ranges are
+    // spread over the warps it has)
+    g->acc_blocks[0] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<1>), g->num_sms);
+    g->acc_blocks[1] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<2>), g->num_sms);
+    g->acc_blocks[2] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<6>), g->num_sms);
+    g->acc_blocks[3] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<24>), g->num_sms);
     switch (nl) {
     case 1: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<1, MODE_SCATTER>), g->num_sms); break;
     case 2: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<2, MODE_SCATTER>), g->num_sms); break;

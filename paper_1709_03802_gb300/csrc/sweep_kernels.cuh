@@ -1231,7 +1231,8 @@ __device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, 
         }
         __syncwarp();
         const int cntj = static_cast<int>(min(static_cast<long long>(kWarp), end - b));
-        for (int j = 0; j < cntj; ++j) {
+        int j = 0;
+        while (j < cntj) {
             if (b + j >= nb) {  // warp-uniform: the next cell's records begin
                 flush(cur);
                 cur = advance_cell(off, n_leaf, cur, b + j, lane);
@@ -1239,14 +1240,35 @@ __device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, 
             }
             const ulonglong2 ra = sh_rec[j], rb = sh_rec2[j];
             const unsigned long long cx = ra.x, cy = ra.y, cz = rb.x, cc = rb.y;
+            if (j + 1 < cntj && b + j + 1 < nb) {
+                // two records of the same cell: independent weight chains
+                const ulonglong2 ra1 = sh_rec[j + 1], rb1 = sh_rec2[j + 1];
+                const unsigned long long dx = ra1.x, dy = ra1.y, dz = rb1.x, dc = rb1.y;
 #pragma unroll
-            for (int i = 0; i < NP2; ++i) {
-                unsigned long long t = f2_fma(mx[i], cx, B2);
-                t = f2_fma(my[i], cy, t);
-                t = f2_fma(mz[i], cz, t);
-                const float2 tv = f2_unpack(t);
-                const unsigned long long rr = f2_pack(make_float2(hg_rsqrt(tv.x), hg_rsqrt(tv.y)));
-                acc[i] = f2_fma(cc, f2_mul(f2_mul(rr, rr), rr), acc[i]);
+                for (int i = 0; i < NP2; ++i) {
+                    unsigned long long t = f2_fma(mx[i], cx, B2), u = f2_fma(mx[i], dx, B2);
+                    t = f2_fma(my[i], cy, t);
+                    u = f2_fma(my[i], dy, u);
+                    t = f2_fma(mz[i], cz, t);
+                    u = f2_fma(mz[i], dz, u);
+                    const float2 tv = f2_unpack(t), uv = f2_unpack(u);
+                    const unsigned long long rt = f2_pack(make_float2(hg_rsqrt(tv.x), hg_rsqrt(tv.y)));
+                    const unsigned long long ru = f2_pack(make_float2(hg_rsqrt(uv.x), hg_rsqrt(uv.y)));
+                    const unsigned long long wt = f2_mul(f2_mul(rt, rt), rt), wu = f2_mul(f2_mul(ru, ru), ru);
+                    acc[i] = f2_fma(dc, wu, f2_fma(cc, wt, acc[i]));
+                }
+                j += 2;
+            } else {
+#pragma unroll
+                for (int i = 0; i < NP2; ++i) {
+                    unsigned long long t = f2_fma(mx[i], cx, B2);
+                    t = f2_fma(my[i], cy, t);
+                    t = f2_fma(mz[i], cz, t);
+                    const float2 tv = f2_unpack(t);
+                    const unsigned long long rr = f2_pack(make_float2(hg_rsqrt(tv.x), hg_rsqrt(tv.y)));
+                    acc[i] = f2_fma(cc, f2_mul(f2_mul(rr, rr), rr), acc[i]);
+                }
+                j += 1;
             }
         }
         __syncwarp();
@@ -1255,7 +1277,7 @@ __device__ inline void accumulate_range(const DevGrid &G, int l, long long beg, 
 }
 
 template <int PPL>
-__global__ void __launch_bounds__(kBlock) cell_accumulate_kernel(const DevGrid G, int l, const PipeDev *pd,
+__global__ void __launch_bounds__(kBlock, PPL <= 6 ? 3 : 1) cell_accumulate_kernel(const DevGrid G, int l, const PipeDev *pd,
                                                                  const int *n_sorted, const unsigned *off,
                                                                  int n_leaf, const float4 *sdir,
                                                                  const float *scoef, long long cap, int packed,
@@ -1265,11 +1287,14 @@ __global__ void __launch_bounds__(kBlock) cell_accumulate_kernel(const DevGrid G
     if (!pd->flush) return;
     const long long n = static_cast<long long>(*n_sorted);  // records bucketed (holes excluded)
     const long long warps = static_cast<long long>(gridDim.x) * (blockDim.x / kWarp);
-    const long long nranges = (n + kAccRange - 1) / kAccRange;
+    // ranges of kAccRange records, fewer records per range (down to 256) when
+    // the flush is too small to give every warp four ranges
+    const long long per = max(256ll, min(static_cast<long long>(kAccRange), (n + 4 * warps - 1) / (4 * warps)));
+    const long long nranges = (n + per - 1) / per;
     const int lane = threadIdx.x & 31;
     for (long long w = blockIdx.x * static_cast<long long>(blockDim.x / kWarp) + (threadIdx.x >> 5); w < nranges;
          w += warps) {
-        const long long beg = w * kAccRange, end = min(n, beg + kAccRange);
+        const long long beg = w * per, end = min(n, beg + per);
         accumulate_range<PPL>(G, l, beg, end, n, off, n_leaf, sdir, scoef, cap, packed != 0, pend, lane,
                               sh_rec[threadIdx.x >> 5], sh_rec2[threadIdx.x >> 5]);
     }
