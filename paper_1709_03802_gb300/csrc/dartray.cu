@@ -186,18 +186,18 @@ int fetch_host(std::vector<T> &dst, const T *src, size_t count, bool on_device) 
     return DARTRAY_OK;
 }
 
-int occupancy_blocks(const void *kernel, int num_sms) {
+int occupancy_blocks(const void *kernel, int num_sms, int block = kBlock) {
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
     return std::max(1, per_sm) * num_sms;
 }
 
 template <int NL>
 int launch_march_nl(dartray_grid *g, cudaStream_t st, int mode, const MarchArgs &A) {
     const int blocks = g->march_blocks;
-    if (mode == MODE_LL) march_kernel<NL, MODE_LL><<<blocks, kBlock, 0, st>>>(g->G, A);
-    else if (mode == MODE_DIRECT) march_kernel<NL, MODE_DIRECT><<<blocks, kBlock, 0, st>>>(g->G, A);
-    else march_kernel<NL, MODE_SCATTER><<<blocks, kBlock, 0, st>>>(g->G, A);
+    if (mode == MODE_LL) march_kernel<NL, MODE_LL><<<blocks, kMarchBlock, 0, st>>>(g->G, A);
+    else if (mode == MODE_DIRECT) march_kernel<NL, MODE_DIRECT><<<blocks, kMarchBlock, 0, st>>>(g->G, A);
+    else march_kernel<NL, MODE_SCATTER><<<blocks, kMarchBlock, 0, st>>>(g->G, A);
     ++g->launches;
     CK(cudaGetLastError());
     return DARTRAY_OK;
@@ -932,11 +932,11 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
     g->acc_blocks[2] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<6>), g->num_sms);
     g->acc_blocks[3] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<24>), g->num_sms);
     switch (nl) {
-    case 1: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<1, MODE_SCATTER>), g->num_sms); break;
-    case 2: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<2, MODE_SCATTER>), g->num_sms); break;
-    case 4: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<4, MODE_SCATTER>), g->num_sms); break;
-    case 8: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<8, MODE_SCATTER>), g->num_sms); break;
-    default: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<16, MODE_SCATTER>), g->num_sms); break;
+    case 1: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<1, MODE_SCATTER>), g->num_sms, kMarchBlock); break;
+    case 2: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<2, MODE_SCATTER>), g->num_sms, kMarchBlock); break;
+    case 4: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<4, MODE_SCATTER>), g->num_sms, kMarchBlock); break;
+    case 8: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<8, MODE_SCATTER>), g->num_sms, kMarchBlock); break;
+    default: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<16, MODE_SCATTER>), g->num_sms, kMarchBlock); break;
     }
     if (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess ||
         cudaEventCreate(&g->mev0) != cudaSuccess || cudaEventCreate(&g->mev1) != cudaSuccess)

@@ -10,6 +10,9 @@ namespace dartray {
 
 enum { MODE_LL = 0, MODE_DIRECT = 1, MODE_SCATTER = 2 };
 constexpr int kBlock = 256;
+// marcher blocks: 128 threads, 5 per SM with one wavelength (96 registers)
+constexpr int kMarchBlock = 128;
+constexpr int kMarchMinBlocks1 = 5;
 constexpr int kPixTab = 1020;  // pixel centres of levels 0..3 (j_sca levels)
 
 struct MarchArgs {
@@ -155,15 +158,15 @@ struct Ledger {
  *     pixel loop of each depositing lane.
  */
 template <int NL, int MODE>
-__global__ void __launch_bounds__(kBlock, NL == 1 ? 3 : (NL <= 4 ? 2 : 1)) march_kernel(const DevGrid G, const MarchArgs A) {
+__global__ void __launch_bounds__(kMarchBlock, NL == 1 ? kMarchMinBlocks1 : (NL <= 4 ? 2 : 1)) march_kernel(const DevGrid G, const MarchArgs A) {
     __shared__ float4 sh_pix[kPixTab];
     __shared__ double sh_led[LG_N][kMaxLambda];
     __shared__ unsigned long long sh_cnt[CT_N];
-    __shared__ ChunkState sh_chunk[kBlock / kWarp][3];  // high list, low list, deposit records
+    __shared__ ChunkState sh_chunk[kMarchBlock / kWarp][3];  // high list, low list, deposit records
     for (int i = threadIdx.x; i < kPixTab; i += blockDim.x) sh_pix[i] = G.dirtab[i];
     for (int i = threadIdx.x; i < LG_N * kMaxLambda; i += blockDim.x) (&sh_led[0][0])[i] = 0.0;
     if (threadIdx.x < CT_N) sh_cnt[threadIdx.x] = 0;
-    if (threadIdx.x < (kBlock / kWarp) * 3) {
+    if (threadIdx.x < (kMarchBlock / kWarp) * 3) {
         ChunkState &c = (&sh_chunk[0][0])[threadIdx.x];
         c.base = 0;
         c.left = 0;
