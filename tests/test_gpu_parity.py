@@ -166,6 +166,12 @@ def test_small_queues_recover_by_batching():
     Ua, Ub = a.rfed()[0], b.rfed()[0]
     assert sa["crossings"] == sb["crossings"]
     assert np.abs(Ua - Ub).max() <= 1e-5 * Ub.max()
+    # a second call sizes its batches from the first call's heaviest batch:
+    # no more restarts than the first call, the same result
+    sa2 = a.direct()
+    assert sa2["restarts"] <= sa["restarts"]
+    assert sa2["crossings"] == sa["crossings"]
+    assert np.abs(a.rfed()[0] - Ua).max() <= 1e-5 * Ub.max()
 
 
 def test_device_buffers_and_state_roundtrip(tmp_path):
