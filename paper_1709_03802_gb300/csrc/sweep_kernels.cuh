@@ -55,17 +55,6 @@ struct MarchArgs {
 // beam solid angle 4 pi / (12 4^k), scaled exactly from float(pi/3)
 __device__ inline float omega_of(int k) { return ldexpf(static_cast<float>(kPi / 3.0), -2 * k); }
 
-// Warp-aggregated append: returns this lane's slot (valid only where want).
-__device__ inline unsigned long long warp_append(bool want, unsigned long long *counter, int lane) {
-    const unsigned m = __ballot_sync(kFull, want);
-    if (!m) return 0;
-    const int leader = __ffs(m) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(counter, static_cast<unsigned long long>(__popc(m)));
-    base = __shfl_sync(kFull, base, leader);
-    return base + __popc(m & ((1u << lane) - 1u));
-}
-
 // Output lists are filled in per-warp chunks: a warp reserves `chunk` slots
 // with one atomic and hands them out over many iterations, so appends rarely
 // wait on a returning atomic.  Slots a warp leaves unused are holes, marked
@@ -1030,16 +1019,12 @@ __global__ void labs_kernel(const DevGrid G, const float *U, float c_light, floa
 }
 
 // ------------------------------------------------------- deferred deposit
-// Records of depositing crossings are bucketed by cell (count, scan,
-// scatter) and each cell's scattering source-function row is accumulated by
-// one warp holding the row in registers: pending[c][q] += sum over records of
-// coef * Phi(n_q . n) / A, with Phi = A (1 + g^2 - 2 g mu)^(-3/2) (Eq. 4; the
-// constant A cancels against the row normalisation already in coef).
-__global__ void rec_count_kernel(const unsigned *cell, long long n, unsigned *cnt) {
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x)
-        atomicAdd(&cnt[cell[i]], 1u);
-}
+// Records of depositing crossings are bucketed by cell (the marcher counts
+// them per cell; scan; scatter) and each cell's scattering source-function
+// row is accumulated by one warp holding the row in registers:
+// pending[c][q] += sum over records of coef * Phi(n_q . n) / A, with
+// Phi = A (1 + g^2 - 2 g mu)^(-3/2) (Eq. 4; the constant A cancels against
+// the row normalisation already in coef).
 
 // exclusive scan of per-cell counts: block totals, then per-element offsets
 __global__ void scan_apply_kernel(const PipeDev *pd, const unsigned *cnt, int n, const int *block_off, unsigned *off,
