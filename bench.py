@@ -133,6 +133,8 @@ def run_step(gpu, grid):
     st = gpu.direct()
     cross = st["crossings"]
     march_ms = st["march_ms"]
+    march_sum_ms = st["march_sum_ms"]
+    march_launches = st["march_launches"]
     flush_ms = st["flush_ms"]
     march_cross = st["crossings"]
     jpix = st["jsca_pixels"]
@@ -144,6 +146,8 @@ def run_step(gpu, grid):
         it += 1
         cross += s2["crossings"]
         march_ms += s2["march_ms"]
+        march_sum_ms += s2["march_sum_ms"]
+        march_launches += s2["march_launches"]
         flush_ms += s2["flush_ms"]
         march_cross += s2["crossings"]
         jpix += s2["jsca_pixels"]
@@ -153,7 +157,8 @@ def run_step(gpu, grid):
             break
     m = gpu.map(OBSERVER, MAP_K, max_sub=MAP_SUB, use_jsca=True)
     launches += 1
-    return dict(crossings=cross, march_ms=march_ms, flush_ms=flush_ms, march_crossings=march_cross, jsca_pixels=jpix,
+    return dict(crossings=cross, march_ms=march_ms, march_sum_ms=march_sum_ms, march_launches=march_launches,
+                flush_ms=flush_ms, march_crossings=march_cross, jsca_pixels=jpix,
                 iters=it, iter_ms=it_ms, launches=launches, map=m)
 
 
@@ -329,10 +334,17 @@ def main():
     npx = 12 * 4 ** gpu.k_lam[0]
     alg_bytes = sum(r["march_crossings"] * bytes_per_crossing(nl) + 24 * r["jsca_pixels"] / npx for r in results)
     peak, peak_src = peaks()
-    achieved = alg_bytes / (march_ms / 1e3) / 1e9 if march_ms > 0 else None
+    # per launch: algorithmic bytes / the launch's CUDA-event span on its
+    # stream, averaged over the launches (= all bytes / summed spans; a span
+    # includes any wait for SMs held by the other pipeline's kernels)
+    march_sum_ms = sum(r["march_sum_ms"] for r in results)
+    launches = sum(r["march_launches"] for r in results)
+    achieved = alg_bytes / (march_sum_ms / 1e3) / 1e9 if march_sum_ms > 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
                 "kernel": "march_kernel (ray marcher)", "peak_source": peak_src,
+                "launches": launches, "avg_launch_ms": march_sum_ms / launches if launches else None,
+                "achieved_over_busy_union": alg_bytes / (march_ms / 1e3) / 1e9 if march_ms > 0 else None,
                 "kernel_busy_share_of_step": march_ms / total_ms if total_ms else None,
                 "deposit_flush_share_of_step": (sum(r["flush_ms"] for r in results) / total_ms
                                                 if total_ms else None)}

@@ -143,6 +143,8 @@ typedef struct dartray_stats {
                              low-list merge, flush, wave advance) of either pipeline */
     int64_t restarts;     /* phase restarts with smaller source batches after a ray-queue
                              overflow (the result does not depend on them) */
+    double march_sum_ms;  /* with params.profile: sum over ray-march launches of each
+                             launch's event span on its stream (march_launches of them) */
 } dartray_stats;
 
 /* Fill *p with the defaults above (r_pre is set when the grid is created if

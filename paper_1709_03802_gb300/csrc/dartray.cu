@@ -131,7 +131,7 @@ struct dartray_grid {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long rec_cap = 0;
     cudaEvent_t mev0 = nullptr, mev1 = nullptr;  // around each march launch (profile mode)
-    double march_ms = 0.0, flush_ms = 0.0, busy_ms = 0.0;
+    double march_ms = 0.0, flush_ms = 0.0, busy_ms = 0.0, march_sum_ms = 0.0;
     long long march_launches = 0, restarts = 0;
     // peak rays per source of each mode's waves, learned by earlier calls: the
     // first batch of a phase is sized with it (0: not yet known)
@@ -299,6 +299,12 @@ struct SpanTiming {
             pool.push_back(pr.second);
         }
         pending[i].clear();
+    }
+    // summed lengths of the spans
+    double sum_ms() const {
+        double tot = 0.0;
+        for (auto &sp : spans) tot += sp.second - sp.first;
+        return tot;
     }
     // length of the union of all spans
     double busy_ms() {
@@ -630,6 +636,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
             }
             if (tm) {
                 g->march_ms += tm->march.busy_ms();
+                g->march_sum_ms += tm->march.sum_ms();
                 g->flush_ms += tm->flush.busy_ms();
                 // the final flushes count as busy time too
                 for (auto &sp : tm->flush.spans) tm->wave.spans.push_back(sp);
@@ -958,7 +965,7 @@ int dartray_direct(dartray_grid *g, dartray_stats *stats) {
     CK(cudaMemsetAsync(g->d_jtot, 0, g->sca_len * sizeof(float), g->stream));
     g->cur = 0;  // step 2 deposits into d_pend[1]
     const long long l0 = g->launches;
-    g->march_ms = g->flush_ms = g->busy_ms = 0.0;
+    g->march_ms = g->flush_ms = g->busy_ms = g->march_sum_ms = 0.0;
     g->march_launches = g->restarts = 0;
     CK(cudaEventRecord(g->ev0, g->stream));
     PhaseResult r1{}, r2{};
@@ -979,6 +986,7 @@ int dartray_direct(dartray_grid *g, dartray_stats *stats) {
         stats->flush_ms = g->flush_ms;
         stats->busy_ms = g->busy_ms;
         stats->restarts = g->restarts;
+        stats->march_sum_ms = g->march_sum_ms;
     }
     return DARTRAY_OK;
 }
@@ -991,7 +999,7 @@ int dartray_scatter_iter(dartray_grid *g, double *remaining_frac, dartray_stats 
     if (rc) return rc;
     CK(cudaMemsetAsync(g->d_st, 0, sizeof(DevStats), g->stream));
     const long long l0 = g->launches;
-    g->march_ms = g->flush_ms = g->busy_ms = 0.0;
+    g->march_ms = g->flush_ms = g->busy_ms = g->march_sum_ms = 0.0;
     g->march_launches = g->restarts = 0;
     CK(cudaEventRecord(g->ev0, g->stream));
     PhaseResult r{};
@@ -1010,6 +1018,7 @@ int dartray_scatter_iter(dartray_grid *g, double *remaining_frac, dartray_stats 
         stats->flush_ms = g->flush_ms;
         stats->busy_ms = g->busy_ms;
         stats->restarts = g->restarts;
+        stats->march_sum_ms = g->march_sum_ms;
     }
     return DARTRAY_OK;
 }

@@ -56,7 +56,7 @@ class dartray_stats(C.Structure):
                [("f_u", C.c_double), ("l_sca2", C.c_double), ("gpu_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("march_ms", C.c_double), ("march_launches", C.c_int64),
                 ("jsca_pixels", C.c_int64), ("flush_ms", C.c_double), ("busy_ms", C.c_double),
-               ("restarts", C.c_int64)]
+               ("restarts", C.c_int64), ("march_sum_ms", C.c_double)]
 
     def to_dict(self, n_lambda=1):
         out = {}
