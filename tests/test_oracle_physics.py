@@ -301,3 +301,50 @@ def test_scattering_deposit_and_reemission_directions():
     for name, d in detectors.items():
         assert abs(dU[d] / ref[name] - 1) < 1e-7, (name, dU[d], ref[name])
     assert dU[detectors["forward"]] > 30 * dU[detectors["backward"]]
+
+
+def test_map_directions_attenuation_and_scattered_light():
+    """Internal-observer map (Sect. 2, end; I_obs = I_0 e^{-tau}) recomputed
+    from the definitions, one point per cell: the emitting cell lands in the
+    pixel of the direction from the observer to it with S e^{-tau} / d^2 /
+    Omega_pix, tau along its path through the scatterer's corner;
+    the scatterer adds j_sca,total[pixel of the direction from it to the
+    observer] / Omega_k, attenuated along its own half chord.  A sign error in
+    either direction, or a missing attenuation, fails it (the flux sum of the
+    empty-medium pin does not see directions)."""
+    n, cell, k0, nside_k = 9, 0.25, 6, 3
+    base = synth.small_sphere(n, cell=cell, radius=100.0, tau_radial=0.0, albedo=0.6, g=0.6)
+    centre = base.leaf_centre
+    scat = int(np.nonzero(np.all(np.isclose(centre, [0.5, 0.0, 0.0]), axis=1))[0][0])
+    kr = base.kappa_rho.copy()
+    kr[scat, 0] = 0.04
+    grid = base.with_lambda(kr, base.emissivity, base.albedo, base.g)
+    o = oracle.Oracle(grid, oracle.OracleParams(k0=k0, **BRUTE))
+    o.direct()
+    k = int(o.k_lam[0])
+    jtot = o.jsca(0, "total")
+    # ahead of the scatterer and off the axis, in an empty cell: the light
+    # scattered toward it is forward light, the reverse direction backward
+    obs = np.array([1.0, 0.3, 0.03])
+    m = o.map(obs, nside_k, max_sub=0, use_jsca=True)[0]
+
+    om_pix, om_k = 4 * math.pi / (12 * 4 ** nside_k), 4 * math.pi / (12 * 4 ** k)
+    src = int(np.nonzero(grid.emissivity[:, 0])[0][0])
+    krs = float(grid.kappa_rho[scat, 0])
+    expect = np.zeros_like(m)
+    # the emitting cell: its path to the observer clips the scatterer
+    v = obs - centre[src]
+    d = np.linalg.norm(v)
+    tau = krs * _chord(centre[src], v / d, grid.leaf_lo[scat], grid.leaf_lo[scat] + cell)
+    assert tau > 0
+    S = float(grid.emissivity[src, 0]) * cell ** 3
+    expect[oracle.vec2pix(nside_k, -v / d)] += S * math.exp(-tau) / d ** 2 / om_pix
+    # the scatterer: scattered light toward the observer, out of its own cell
+    v = obs - centre[scat]
+    d = np.linalg.norm(v)
+    tau = krs * _chord(centre[scat], v / d, grid.leaf_lo[scat], grid.leaf_lo[scat] + cell)
+    I0 = jtot[scat, oracle.vec2pix(k, v / d)] / om_k
+    assert I0 > 10 * jtot[scat, oracle.vec2pix(k, -v / d)] / om_k
+    expect[oracle.vec2pix(nside_k, -v / d)] += I0 * math.exp(-tau) / d ** 2 / om_pix
+    assert np.count_nonzero(expect) == 2
+    assert np.abs(m - expect).max() <= 1e-12 * expect.max()
