@@ -105,3 +105,33 @@ def test_rejects_unsupported_lambda_count():
     d.n_lambda = 3
     rc, msg = _create(d)
     assert rc == -1 and "n_lambda" in msg
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and offsetof of a header struct, from a C program built with
+    the system compiler against include/dartray.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = [f'printf("%zu\\n", sizeof({struct}));']
+    lines += [f'printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"dartray.h\"\n"
+                   "int main(void) {\n" + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    return vals[0], vals[1:]
+
+
+@pytest.mark.parametrize("cls", [dr.dartray_grid_desc, dr.dartray_params, dr.dartray_stats],
+                         ids=lambda c: c.__name__)
+def test_binding_structs_match_the_header_layout(cls, tmp_path):
+    """The ctypes mirrors of the ABI structs have the header's size and the
+    same offset for every field."""
+    fields = [name for name, _ in cls._fields_]
+    size, offsets = _c_layout(cls.__name__, fields, tmp_path)
+    assert C.sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offsets
