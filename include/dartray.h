@@ -166,7 +166,14 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
 /* Steps 1 and 2 of Sect. 2: U_LL within R_pre, then direct light with ray
  * blocking (Eq. 1), depositing U, and the scattered luminosity into the
  * pending j_sca buffer; afterwards U_LL <- U and j_sca_total += pending.
- * stats may be NULL.  Errors: LIMIT, QUEUE, CUDA. */
+ * stats may be NULL.  Errors: LIMIT, QUEUE, CUDA.
+ *
+ * Sources are traced in batches sized to the ray queues.  A batch whose
+ * waves overflow a queue restarts the phase with smaller batches (counted in
+ * stats->restarts).  The grid keeps, per phase kind, the largest peak wave
+ * per source seen, and later calls size their batches from it, so repeated
+ * calls on one grid do not restart.  None of this changes the result: a
+ * phase is additive over sources. */
 int dartray_direct(dartray_grid *grid, dartray_stats *stats);
 
 /* One scattering iteration (Sect. 2): the pending scattered luminosity of the
