@@ -348,3 +348,31 @@ def test_map_directions_attenuation_and_scattered_light():
     expect[oracle.vec2pix(nside_k, -v / d)] += I0 * math.exp(-tau) / d ** 2 / om_pix
     assert np.count_nonzero(expect) == 2
     assert np.abs(m - expect).max() <= 1e-12 * expect.max()
+
+
+def test_step1_rpre_cut_is_exact_in_an_empty_medium():
+    """Step 1 (Sect. 2): rays stop at the first crossing that starts at
+    d >= R_pre.  In an empty medium without splitting or blocking, a cell lying
+    wholly within R_pre of the source therefore receives exactly the U of the
+    unrestricted direct step, a cell wholly beyond it receives nothing, and
+    every ray ends in the cut ledger (none escapes, none is absorbed)."""
+    n, cell, k0, R = 9, 0.25, 6, 0.6
+    grid = synth.small_sphere(n, cell=cell, radius=100.0, tau_radial=0.0, albedo=0.6, g=0.6)
+    o = oracle.Oracle(grid, oracle.OracleParams(k0=k0, a_rt=0.0, r_pre=R, n_rays_min=0, merge=0))
+    o.run_phase(0)
+    U_LL = o.U_LL.copy()
+    led, _ = o.stats()
+    full = oracle.Oracle(grid, oracle.OracleParams(k0=k0, **BRUTE))
+    full.direct()
+    U = full.rfed()[0][:, 0]
+
+    lo, hi = grid.leaf_lo, grid.leaf_lo + cell
+    corners = np.stack([np.where(np.array([(c >> a) & 1 for a in range(3)]) == 1, hi, lo) for c in range(8)])
+    dmax = np.sqrt((corners ** 2).sum(-1)).max(0)
+    dmin = np.sqrt((np.clip(0.0, lo, hi) ** 2).sum(1))  # nearest point of the box to the source
+    within, beyond = dmax < R, dmin > R
+    assert within.sum() >= 7 and beyond.sum() >= 100
+    assert np.abs(U_LL[within] - U[within]).max() <= 1e-12 * U[within].max()
+    assert np.all(U_LL[beyond] == 0.0)
+    assert led["escaped"][0] == 0.0 and led["absorbed"][0] == 0.0
+    assert abs(led["cut"][0] / led["emitted"][0] - 1) < 1e-12
