@@ -376,3 +376,63 @@ def test_step1_rpre_cut_is_exact_in_an_empty_medium():
     assert np.all(U_LL[beyond] == 0.0)
     assert led["escaped"][0] == 0.0 and led["absorbed"][0] == 0.0
     assert abs(led["cut"][0] / led["emitted"][0] - 1) < 1e-12
+
+
+def _cells_along(grid, x0, n, start):
+    """Leaves crossed by the ray x0 + t n after leaving leaf `start`, in order,
+    with their chords (a point just beyond each exit picks the next leaf, so
+    exits through an edge or corner go diagonally)."""
+    lo, hi = grid.leaf_lo, grid.leaf_lo + grid.leaf_size[:, None]
+    out, leaf, t_in = [], start, 0.0
+    while True:
+        with np.errstate(divide="ignore"):
+            tt = np.where(n > 0, (hi[leaf] - x0) / n, np.where(n < 0, (lo[leaf] - x0) / n, np.inf))
+        t_out = tt.min()
+        out.append((leaf, t_out - t_in))
+        p = x0 + n * (t_out + 1e-9)
+        ids = np.nonzero(np.all((lo <= p) & (p < hi), axis=1))[0]
+        if ids.size == 0:
+            return out
+        leaf, t_in = int(ids[0]), t_out
+
+
+def test_blocking_decisions_of_eq1_in_an_empty_medium():
+    """Eq. 1 with the Sect. 3.5 dU: a ray is blocked at the first crossing
+    outside its source cell where <I> Omega_INT L / (V c) = S / (r^2 c) falls
+    below f_U U_LL, with f_U = 4 a_RT / N_s and U_LL from step 1.  Every
+    decision is recomputed along each ray's cells, and so is the direct-light
+    U of every cell.  f_U sits among the per-ray ratios, at least 5e-5 away
+    from each, so about half the rays are blocked and rounding decides
+    nothing."""
+    n, cell, k0, R, f_u = 9, 0.25, 5, 0.6, 0.95265
+    grid = synth.small_sphere(n, cell=cell, radius=100.0, tau_radial=0.0, albedo=0.6, g=0.6)
+    o = oracle.Oracle(grid, oracle.OracleParams(k0=k0, a_rt=f_u / 4, r_pre=R, n_rays_min=0, merge=0))
+    o.run_phase(0)
+    U_LL = o.U_LL.copy()
+    o.direct()
+    U = o.rfed()[0][:, 0]
+    led, cnt = o.stats()
+    assert abs(o.f_u - f_u) < 1e-15
+
+    src = int(np.nonzero(grid.emissivity[:, 0])[0][0])
+    xs = grid.leaf_centre[src]
+    S = float(grid.emissivity[src, 0]) * cell ** 3
+    om0 = 4 * math.pi / (12 * 4 ** k0)
+    V = cell ** 3
+    U_pred = np.zeros(grid.n_leaf)
+    blocked, margin = 0, np.inf
+    for p in range(12 * 4 ** k0):
+        v = oracle.pix2vec(k0, p)
+        for leaf, ds in _cells_along(grid, xs, v, src):
+            if leaf != src and U_LL[leaf] > 0:
+                dU = S / ((grid.leaf_centre[leaf] - xs) ** 2).sum()
+                margin = min(margin, abs(dU / (f_u * U_LL[leaf]) - 1))
+                if dU < f_u * U_LL[leaf]:
+                    blocked += 1
+                    break
+            U_pred[leaf] += S * om0 * ds / V
+    assert margin > 5e-5
+    assert 0.3 < blocked / (12 * 4 ** k0) < 0.9
+    assert cnt["blocks"] == blocked
+    assert abs(led["blocked"][0] / (blocked * S * om0) - 1) < 1e-12
+    assert np.abs(U - U_pred).max() <= 1e-9 * U_pred.max()
