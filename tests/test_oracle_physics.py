@@ -378,12 +378,12 @@ def test_step1_rpre_cut_is_exact_in_an_empty_medium():
     assert abs(led["cut"][0] / led["emitted"][0] - 1) < 1e-12
 
 
-def _cells_along(grid, x0, n, start):
-    """Leaves crossed by the ray x0 + t n after leaving leaf `start`, in order,
-    with their chords (a point just beyond each exit picks the next leaf, so
-    exits through an edge or corner go diagonally)."""
+def _cells_along(grid, x0, n, start, t0=0.0):
+    """Leaves crossed by the ray x0 + t n from t = t0 in leaf `start`, in
+    order, with their chords (a point just beyond each exit picks the next
+    leaf, so exits through an edge or corner go diagonally)."""
     lo, hi = grid.leaf_lo, grid.leaf_lo + grid.leaf_size[:, None]
-    out, leaf, t_in = [], start, 0.0
+    out, leaf, t_in = [], start, t0
     while True:
         with np.errstate(divide="ignore"):
             tt = np.where(n > 0, (hi[leaf] - x0) / n, np.where(n < 0, (lo[leaf] - x0) / n, np.inf))
@@ -435,4 +435,52 @@ def test_blocking_decisions_of_eq1_in_an_empty_medium():
     assert 0.3 < blocked / (12 * 4 ** k0) < 0.9
     assert cnt["blocks"] == blocked
     assert abs(led["blocked"][0] / (blocked * S * om0) - 1) < 1e-12
+    assert np.abs(U - U_pred).max() <= 1e-9 * U_pred.max()
+
+
+def test_split_decisions_of_eq2_in_an_empty_medium():
+    """Eq. 2 (Sect. 3.1.1): a ray of level k stops at the first crossing
+    outside its source cell where 4 pi N_rays r^2 > 12 4^k L^2 and its four
+    children (level k+1, pixels 4p..4p+3) restart at the same distance from
+    the source along their own directions, in the cell their direction points
+    into.  The whole ray tree is recomputed in an empty medium without
+    blocking or merging: the split count exactly and the U of every cell to
+    1e-9 (each ray keeps its per-sr intensity; its beam is Omega_k)."""
+    n, cell, k0, nmin = 9, 0.25, 2, 5
+    grid = synth.small_sphere(n, cell=cell, radius=100.0, tau_radial=0.0, albedo=0.6, g=0.6)
+    o = oracle.Oracle(grid, oracle.OracleParams(k0=k0, a_rt=0.0, r_pre=100.0, n_rays_min=nmin, merge=0))
+    o.direct()
+    U = o.rfed()[0][:, 0]
+    led, cnt = o.stats()
+
+    src = int(np.nonzero(grid.emissivity[:, 0])[0][0])
+    xs = grid.leaf_centre[src]
+    S = float(grid.emissivity[src, 0]) * cell ** 3
+    lo, hi = grid.leaf_lo, grid.leaf_lo + cell
+    U_pred = np.zeros(grid.n_leaf)
+    splits = rays = 0
+    stack = [(k0, p, 0.0, src) for p in range(12 * 4 ** k0)]
+    while stack:
+        k, p, t0, start = stack.pop()
+        rays += 1
+        v = oracle.pix2vec(k, p)
+        om = 4 * math.pi / (12 * 4 ** k)
+        t_in = t0  # distance of the segment's start from the source
+        for leaf, ds in _cells_along(grid, xs, v, start, t0):
+            r2 = ((grid.leaf_centre[leaf] - xs) ** 2).sum()
+            if leaf != src and 4 * math.pi * nmin * r2 > 12 * 4 ** k * cell * cell:
+                splits += 1
+                for c in range(4):
+                    w = oracle.pix2vec(k + 1, 4 * p + c)
+                    q = xs + (t_in + 1e-9) * w
+                    child_leaf = int(np.nonzero(np.all((lo <= q) & (q < hi), axis=1))[0][0])
+                    stack.append((k + 1, 4 * p + c, t_in, child_leaf))
+                break
+            U_pred[leaf] += S * om * ds / cell ** 3
+            t_in += ds
+    assert splits > 500
+    # counters cover both phases of the call; step 1 (R_pre beyond the model)
+    # traces the same tree
+    assert cnt["splits"] == 2 * splits and cnt["rays"] == 2 * rays
+    assert abs(led["escaped"][0] / led["emitted"][0] - 1) < 1e-12
     assert np.abs(U - U_pred).max() <= 1e-9 * U_pred.max()
