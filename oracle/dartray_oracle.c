@@ -34,7 +34,11 @@
  * base pixels, rings of constant z, nested (bit-interleaved) indices.
  *
  * Every floating-point quantity is double.  Parity of each function is pinned
- * by tests/test_oracle_*.py against closed forms, brute force and invariants.
+ * by tests/test_oracle_*.py against closed forms, brute force, invariants and
+ * full recomputations of split trees, blocking decisions, scattering
+ * directions and maps -- except the merge of Eq. 3 (the low-list grouping in
+ * or_source and the resumption of unmerged rays): parity unpinned beyond exact energy
+ * conservation through merges and convergence to the brute-force result.
  */
 #include <math.h>
 #include <stdint.h>
