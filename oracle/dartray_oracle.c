@@ -35,10 +35,11 @@
  *
  * Every floating-point quantity is double.  Parity of each function is pinned
  * by tests/test_oracle_*.py against closed forms, brute force, invariants and
- * full recomputations of split trees, blocking decisions, scattering
- * directions and maps -- except the merge of Eq. 3 (the low-list grouping in
- * or_source and the resumption of unmerged rays): parity unpinned beyond exact energy
- * conservation through merges and convergence to the brute-force result.
+ * full recomputations of split trees, merge waves (uniform grids), blocking
+ * decisions, scattering directions and maps.  One part has parity unpinned
+ * beyond exact energy conservation: the end of a resumed ray's merge
+ * suppression when the cell size changes (or_march), which only adaptive
+ * grids exercise.
  */
 #include <math.h>
 #include <stdint.h>

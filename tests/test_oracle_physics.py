@@ -484,3 +484,95 @@ def test_split_decisions_of_eq2_in_an_empty_medium():
     assert cnt["splits"] == 2 * splits and cnt["rays"] == 2 * rays
     assert abs(led["escaped"][0] / led["emitted"][0] - 1) < 1e-12
     assert np.abs(U - U_pred).max() <= 1e-9 * U_pred.max()
+
+
+def _locate_directed(grid, p, n):
+    """Leaf holding p, a point on a face belonging to the cell the direction
+    n points into (the traversal's face convention)."""
+    lo, hi = grid.leaf_lo, grid.leaf_lo + grid.leaf_size[:, None]
+    up = n >= 0
+    ids = np.nonzero(np.all(((p > lo) | ((p == lo) & up)) & ~((p > hi) | ((p == hi) & up)), axis=1))[0]
+    return int(ids[0]) if ids.size else -1
+
+
+def test_merge_waves_of_eq3_in_an_empty_medium():
+    """Eq. 3 with reading A-7 and R-1, recomputed wave by wave in an empty
+    uniform grid without splitting or blocking: a ray goes to the low list at
+    the first crossing (outside its source cell, not its first segment, not
+    while suppressed) where 4 pi N_max r^2 < 12 4^k L^2; after the wave, four
+    siblings that entered their last cell through the same face plane merge
+    into the parent pixel at their mean distance; others resume in that cell
+    on that face with the test suppressed while the cell size stays the same
+    (here: for good).  Exit distances are divided as the traversal divides
+    them, so ties (edge and corner exits) agree exactly; U agrees bit for bit
+    and every counter matches (the call traces the same tree in both phases,
+    R_pre lying beyond the model)."""
+    n, cell, k0, nmax = 9, 0.25, 5, 40
+    grid = synth.small_sphere(n, cell=cell, radius=100.0, tau_radial=0.0, albedo=0.6, g=0.6)
+    o = oracle.Oracle(grid, oracle.OracleParams(k0=k0, a_rt=0.0, r_pre=100.0, n_rays_min=0, n_rays_max=nmax,
+                                                merge=1))
+    o.direct()
+    U = o.rfed()[0][:, 0]
+    _, cnt = o.stats()
+
+    lo, hi = grid.leaf_lo, grid.leaf_lo + cell
+    src = int(np.nonzero(grid.emissivity[:, 0])[0][0])
+    xs = grid.leaf_centre[src]
+    S = float(grid.emissivity[src, 0]) * cell ** 3
+    merge_c = 4.0 * math.pi * nmax
+    U_pred = np.zeros(grid.n_leaf)
+    tally = dict(rays=0, lows=0, merges=0, resumes=0, escapes=0)
+
+    def march(ray):
+        lev, pix, d = ray["lev"], ray["pix"], ray["d"]
+        v = oracle.pix2vec(lev, pix)
+        om, beam = 4 * math.pi / (12 * 4 ** lev), 12.0 * 4.0 ** lev
+        if ray["kind"] == "resumed":
+            leaf, entry = ray["leaf"], ray["plane"]
+        else:
+            leaf, entry = _locate_directed(grid, xs + d * v, v), (-1, 0.0)
+        supp, first = ray["supp"], True
+        tally["rays"] += 1
+        while True:
+            b = np.where(v > 0, hi[leaf], lo[leaf])
+            with np.errstate(divide="ignore"):
+                t = np.where(v != 0, (b - xs) / v, np.inf)
+            te = t.min()
+            r2 = float(((lo[leaf] + 0.5 * cell - xs) ** 2).sum())
+            if leaf != src and lev > 0 and not first and cell != supp and merge_c * r2 < beam * cell * cell:
+                tally["lows"] += 1
+                return dict(lev=lev, pix=pix, d=d, plane=entry, leaf=leaf)
+            U_pred[leaf] += S * om * (te - d if te > d else 0.0) / cell ** 3
+            d = max(te, d)
+            tie = t == te
+            ax = int(np.argmax(tie))
+            entry = (ax, float(b[ax]))
+            leaf = _locate_directed(grid, np.where(tie, b, np.clip(xs + te * v, lo[leaf], hi[leaf])), v)
+            if leaf < 0:
+                tally["escapes"] += 1
+                return None
+            first = False
+
+    wave = [dict(lev=k0, pix=p, d=0.0, kind="seed", supp=0.0) for p in range(12 * 4 ** k0)]
+    while wave:
+        low = sorted((r for r in map(march, wave) if r is not None), key=lambda r: (r["lev"], r["pix"]))
+        wave = []
+        i = 0
+        while i < len(low):
+            j = i
+            while j < len(low) and (low[j]["lev"], low[j]["pix"] >> 2) == (low[i]["lev"], low[i]["pix"] >> 2):
+                j += 1
+            grp = low[i:j]
+            if len(grp) == 4 and all(g["plane"] == grp[0]["plane"] for g in grp):
+                tally["merges"] += 1
+                wave.append(dict(lev=grp[0]["lev"] - 1, pix=grp[0]["pix"] >> 2,
+                                 d=0.25 * sum(g["d"] for g in grp), kind="merged", supp=0.0))
+            else:
+                tally["resumes"] += len(grp)
+                wave += [dict(g, kind="resumed", supp=cell) for g in grp]
+            i = j
+
+    assert tally["merges"] > 1000 and tally["resumes"] > 500
+    for name, v in tally.items():
+        assert cnt[name] == 2 * v, name
+    assert np.array_equal(U, U_pred)
