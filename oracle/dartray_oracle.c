@@ -35,11 +35,9 @@
  *
  * Every floating-point quantity is double.  Parity of each function is pinned
  * by tests/test_oracle_*.py against closed forms, brute force, invariants and
- * full recomputations of split trees, merge waves (uniform grids), blocking
- * decisions, scattering directions and maps.  One part has parity unpinned
- * beyond exact energy conservation: the end of a resumed ray's merge
- * suppression when the cell size changes (or_march), which only adaptive
- * grids exercise.
+ * full recomputations of split trees, merge waves (on a uniform grid and on
+ * one where the end of a resumed ray's suppression decides merges), blocking
+ * decisions, scattering directions and maps.
  */
 #include <math.h>
 #include <stdint.h>

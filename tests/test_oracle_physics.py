@@ -385,7 +385,7 @@ def _cells_along(grid, x0, n, start, t0=0.0):
     lo, hi = grid.leaf_lo, grid.leaf_lo + grid.leaf_size[:, None]
     out, leaf, t_in = [], start, t0
     while True:
-        with np.errstate(divide="ignore"):
+        with np.errstate(divide="ignore", invalid="ignore"):
             tt = np.where(n > 0, (hi[leaf] - x0) / n, np.where(n < 0, (lo[leaf] - x0) / n, np.inf))
         t_out = tt.min()
         out.append((leaf, t_out - t_in))
@@ -495,33 +495,26 @@ def _locate_directed(grid, p, n):
     return int(ids[0]) if ids.size else -1
 
 
-def test_merge_waves_of_eq3_in_an_empty_medium():
-    """Eq. 3 with reading A-7 and R-1, recomputed wave by wave in an empty
-    uniform grid without splitting or blocking: a ray goes to the low list at
-    the first crossing (outside its source cell, not its first segment, not
-    while suppressed) where 4 pi N_max r^2 < 12 4^k L^2; after the wave, four
-    siblings that entered their last cell through the same face plane merge
-    into the parent pixel at their mean distance; others resume in that cell
-    on that face with the test suppressed while the cell size stays the same
-    (here: for good).  Exit distances are divided as the traversal divides
-    them, so ties (edge and corner exits) agree exactly; U agrees bit for bit
-    and every counter matches (the call traces the same tree in both phases,
-    R_pre lying beyond the model)."""
-    n, cell, k0, nmax = 9, 0.25, 5, 40
-    grid = synth.small_sphere(n, cell=cell, radius=100.0, tau_radial=0.0, albedo=0.6, g=0.6)
-    o = oracle.Oracle(grid, oracle.OracleParams(k0=k0, a_rt=0.0, r_pre=100.0, n_rays_min=0, n_rays_max=nmax,
-                                                merge=1))
-    o.direct()
-    U = o.rfed()[0][:, 0]
-    _, cnt = o.stats()
-
-    lo, hi = grid.leaf_lo, grid.leaf_lo + cell
+def _merge_waves(grid, k0, nmax, reset=True):
+    """Steps of one source's waves with merging only (no split, no blocking,
+    empty medium) after readings A-7 and R-1: a ray goes to the low list at
+    the first crossing -- outside its source cell, not on its first segment,
+    not while suppressed -- where 4 pi N_max r^2 < 12 4^k L^2; after the wave,
+    four siblings that entered their last cell through the same face plane
+    merge into the parent pixel at their mean distance, the others resume in
+    that cell on that face with the test suppressed until the cell size
+    changes.  Exit distances are divided as the traversal divides them, so
+    edge and corner ties agree exactly.  Returns the U deposits, the counters
+    and how often a suppression ended."""
+    lo, sz = grid.leaf_lo, grid.leaf_size
+    hi = lo + sz[:, None]
     src = int(np.nonzero(grid.emissivity[:, 0])[0][0])
-    xs = grid.leaf_centre[src]
-    S = float(grid.emissivity[src, 0]) * cell ** 3
+    xs = lo[src] + 0.5 * sz[src]
+    S = float(grid.emissivity[src, 0]) * sz[src] ** 3
     merge_c = 4.0 * math.pi * nmax
     U_pred = np.zeros(grid.n_leaf)
     tally = dict(rays=0, lows=0, merges=0, resumes=0, escapes=0)
+    ends = [0]
 
     def march(ray):
         lev, pix, d = ray["lev"], ray["pix"], ray["d"]
@@ -534,15 +527,16 @@ def test_merge_waves_of_eq3_in_an_empty_medium():
         supp, first = ray["supp"], True
         tally["rays"] += 1
         while True:
+            L = sz[leaf]
             b = np.where(v > 0, hi[leaf], lo[leaf])
-            with np.errstate(divide="ignore"):
+            with np.errstate(divide="ignore", invalid="ignore"):
                 t = np.where(v != 0, (b - xs) / v, np.inf)
             te = t.min()
-            r2 = float(((lo[leaf] + 0.5 * cell - xs) ** 2).sum())
-            if leaf != src and lev > 0 and not first and cell != supp and merge_c * r2 < beam * cell * cell:
+            r2 = float(((lo[leaf] + 0.5 * L - xs) ** 2).sum())
+            if leaf != src and lev > 0 and not first and L != supp and merge_c * r2 < beam * L * L:
                 tally["lows"] += 1
-                return dict(lev=lev, pix=pix, d=d, plane=entry, leaf=leaf)
-            U_pred[leaf] += S * om * (te - d if te > d else 0.0) / cell ** 3
+                return dict(lev=lev, pix=pix, d=d, plane=entry, leaf=leaf, L=L)
+            U_pred[leaf] += S * om * (te - d if te > d else 0.0) / L ** 3
             d = max(te, d)
             tie = t == te
             ax = int(np.argmax(tie))
@@ -551,6 +545,9 @@ def test_merge_waves_of_eq3_in_an_empty_medium():
             if leaf < 0:
                 tally["escapes"] += 1
                 return None
+            if reset and supp != 0 and sz[leaf] != supp:
+                supp = 0.0
+                ends[0] += 1
             first = False
 
     wave = [dict(lev=k0, pix=p, d=0.0, kind="seed", supp=0.0) for p in range(12 * 4 ** k0)]
@@ -569,10 +566,57 @@ def test_merge_waves_of_eq3_in_an_empty_medium():
                                  d=0.25 * sum(g["d"] for g in grp), kind="merged", supp=0.0))
             else:
                 tally["resumes"] += len(grp)
-                wave += [dict(g, kind="resumed", supp=cell) for g in grp]
+                wave += [dict(g, kind="resumed", supp=g["L"]) for g in grp]
             i = j
+    return U_pred, tally, ends[0]
 
-    assert tally["merges"] > 1000 and tally["resumes"] > 500
+
+def _uniform_one_source():
+    return synth.small_sphere(9, cell=0.25, radius=100.0, tau_radial=0.0, albedo=0.6, g=0.6)
+
+
+def _shell_one_source():
+    """Unit cells with a shell of quarter-size cells around the emitting
+    cell (lo = 0): a ray resumed in a unit cell crosses the shell, where its
+    merge test fails, and meets unit cells again beyond it, where it holds --
+    so the end of the suppression decides merges.  No dust."""
+    xs = np.array([0.5, 0.5, 0.5])
+
+    def refine(lo, s, lev):
+        if lev == 0:
+            return np.ones(lo.shape[0], bool)
+        r = np.sqrt(((lo + 0.5 * s[:, None] - xs) ** 2).sum(1))
+        return (r > 1.3) & (r < 2.3)
+
+    fc, lon, llo, lsz = synth.grids.refine_tree((3, 3, 3), (-3.0, -3.0, -3.0), 2.0, 3, refine)
+    n = llo.shape[0]
+    emis = np.zeros((n, 1))
+    emis[int(np.nonzero(np.all(llo == 0.0, axis=1) & (lsz == 1.0))[0][0]), 0] = 1.0
+    return synth.grids._assemble(((3, 3, 3), (-3.0, -3.0, -3.0), 2.0, fc, lon, llo, lsz),
+                                 np.zeros((n, 1)), emis, [0.6], [0.6], "shell")
+
+
+@pytest.mark.parametrize("make, k0, adaptive", [(_uniform_one_source, 5, False), (_shell_one_source, 4, True)],
+                         ids=["uniform", "shell"])
+def test_merge_waves_of_eq3_in_an_empty_medium(make, k0, adaptive):
+    """Eq. 3 recomputed wave by wave (see _merge_waves) on a uniform grid,
+    where a resumed ray stays suppressed for good, and on an adaptive grid,
+    where suppressions end as rays reach cells of another size: U agrees bit
+    for bit and every counter matches (the call traces the same tree in both
+    phases, R_pre lying beyond the model).  On the adaptive grid the
+    recomputation without the end of the suppression disagrees, so the grid
+    does test that rule."""
+    grid = make()
+    o = oracle.Oracle(grid, oracle.OracleParams(k0=k0, a_rt=0.0, r_pre=1000.0, n_rays_min=0, n_rays_max=40,
+                                                merge=1))
+    o.direct()
+    U = o.rfed()[0][:, 0]
+    _, cnt = o.stats()
+    U_pred, tally, ends = _merge_waves(grid, k0, 40)
+    assert tally["merges"] > 500 and tally["resumes"] > 300
     for name, v in tally.items():
         assert cnt[name] == 2 * v, name
     assert np.array_equal(U, U_pred)
+    if adaptive:
+        assert ends > 100
+        assert not np.array_equal(U, _merge_waves(grid, k0, 40, reset=False)[0])
