@@ -184,14 +184,14 @@ def _cpu_worker(job):
     return cpu_sample(grid, params, stride, offset)
 
 
-def cpu_all_cores(stride, unit):
+def cpu_all_cores(stride, unit, processes=None):
     """The oracle on every host core at once: one process per core, each on
     a disjoint sample of every stride-th source (the method is additive over
     sources, so the samples are independent).  Value = crossings of all
     processes / wall time.  Processes are spawned, never forked after CUDA
     initialisation."""
     import multiprocessing as mp
-    n = os.cpu_count() or 1
+    n = processes or os.cpu_count() or 1
     jobs = [(stride, (i * stride) // n) for i in range(n)]
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
