@@ -37,7 +37,10 @@
  * by tests/test_oracle_*.py against closed forms, brute force, invariants and
  * full recomputations of split trees, merge waves (on a uniform grid and on
  * one where the end of a resumed ray's suppression decides merges), blocking
- * decisions, scattering directions and maps.
+ * decisions, scattering directions and maps; the multi-wavelength branch
+ * (per-wavelength Eq. 1, skipped wavelengths, j_sca blocks per k_lambda,
+ * scattering rays from the largest k_lambda) and point sources by
+ * recomputations too.
  */
 #include <math.h>
 #include <stdint.h>

@@ -27,18 +27,40 @@ COUNTER_NAMES = ("rays", "crossings", "splits", "merges", "blocks", "escapes", "
                  "resumes", "waves", "sources")
 
 
+def _compile(src, out):
+    cc = os.environ.get("CC", "gcc")
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = [cc, "-O2", "-std=c11", "-fno-fast-math", "-ffp-contract=off", "-shared", "-fPIC",
+           "-o", tmp, src, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force=False, openmp=False):
     """Compile the oracle shared library (plain C, -O2, no fast-math)."""
     os.makedirs(_BUILD, exist_ok=True)
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
-    cc = os.environ.get("CC", "gcc")
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [cc, "-O2", "-std=c11", "-fno-fast-math", "-ffp-contract=off", "-shared", "-fPIC",
-           "-o", tmp, _SRC, "-lm"]
-    subprocess.check_call(cmd)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return _compile(_SRC, _LIB_PATH)
+
+
+def build_variant(replacements, folder):
+    """Compile a copy of the oracle with textual replacements (old, new), each
+    of which must occur exactly once, into ``folder``.  Tests use it to plant
+    a mistake in the oracle and check that a pin catches it; the returned
+    path goes to ``Oracle(..., lib_path=...)``."""
+    with open(_SRC) as f:
+        src = f.read()
+    for old, new in replacements:
+        if src.count(old) != 1:
+            raise ValueError(f"replacement target occurs {src.count(old)} times: {old!r}")
+        src = src.replace(old, new)
+    os.makedirs(folder, exist_ok=True)
+    cpath = os.path.join(folder, "dartray_oracle_variant.c")
+    with open(cpath, "w") as f:
+        f.write(src)
+    return _compile(cpath, os.path.join(folder, "liboracle_variant.so"))
 
 
 class _Grid(C.Structure):
@@ -66,34 +88,45 @@ class _State(C.Structure):
                 ("L_sca2", C.c_double), ("f_u", C.c_double), ("n_src", C.c_int32)]
 
 
-def _load():
+_variants = {}
+
+
+def _load(path=None):
     global _lib
     with _lock:
+        if path is not None:
+            if path not in _variants:
+                _variants[path] = _bind(C.CDLL(path))
+            return _variants[path]
         if _lib is None:
-            lib = C.CDLL(build())
-            P = C.c_void_p
-            lib.or_pix2vec.argtypes = [C.c_int, C.c_int64, P]
-            lib.or_vec2pix.argtypes = [C.c_int, P]
-            lib.or_vec2pix.restype = C.c_int64
-            lib.or_hg.argtypes = [C.c_double, C.c_double]
-            lib.or_hg.restype = C.c_double
-            lib.or_k_hp_real.argtypes = [C.c_double, C.c_int]
-            lib.or_k_hp_real.restype = C.c_double
-            lib.or_k_hp.argtypes = [C.c_double, C.c_int, C.c_int]
-            lib.or_locate.argtypes = [P, P, P, P]
-            lib.or_trace.argtypes = [P, P, P, C.c_double, C.c_int, P, P, P]
-            lib.or_setup.argtypes = [P, P, P]
-            lib.or_setup.restype = C.c_int64
-            lib.or_direct.argtypes = [P, P, P]
-            lib.or_scatter_iter.argtypes = [P, P, P, P]
-            lib.or_run_phase.argtypes = [P, P, P, C.c_int]
-            lib.or_tau.argtypes = [P, C.c_int, P, P]
-            lib.or_tau.restype = C.c_double
-            lib.or_map.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, P]
-            lib.or_pending_next.argtypes = [P]
-            lib.or_pending_next.restype = C.c_void_p
-            _lib = lib
+            _lib = _bind(C.CDLL(build()))
     return _lib
+
+
+def _bind(lib):
+    """Argument and result types of the oracle's C entry points."""
+    P = C.c_void_p
+    lib.or_pix2vec.argtypes = [C.c_int, C.c_int64, P]
+    lib.or_vec2pix.argtypes = [C.c_int, P]
+    lib.or_vec2pix.restype = C.c_int64
+    lib.or_hg.argtypes = [C.c_double, C.c_double]
+    lib.or_hg.restype = C.c_double
+    lib.or_k_hp_real.argtypes = [C.c_double, C.c_int]
+    lib.or_k_hp_real.restype = C.c_double
+    lib.or_k_hp.argtypes = [C.c_double, C.c_int, C.c_int]
+    lib.or_locate.argtypes = [P, P, P, P]
+    lib.or_trace.argtypes = [P, P, P, C.c_double, C.c_int, P, P, P]
+    lib.or_setup.argtypes = [P, P, P]
+    lib.or_setup.restype = C.c_int64
+    lib.or_direct.argtypes = [P, P, P]
+    lib.or_scatter_iter.argtypes = [P, P, P, P]
+    lib.or_run_phase.argtypes = [P, P, P, C.c_int]
+    lib.or_tau.argtypes = [P, C.c_int, P, P]
+    lib.or_tau.restype = C.c_double
+    lib.or_map.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, P]
+    lib.or_pending_next.argtypes = [P]
+    lib.or_pending_next.restype = C.c_void_p
+    return lib
 
 
 def _ptr(a):
@@ -238,10 +271,10 @@ class Oracle:
     """Stateful FP64 solver mirroring the library calls: direct(),
     scatter_iter(), rfed(), jsca(), map()."""
 
-    def __init__(self, grid, params: OracleParams | None = None):
+    def __init__(self, grid, params: OracleParams | None = None, lib_path=None):
         self.grid = grid
         self.params = params or OracleParams()
-        self._lib = _load()
+        self._lib = _load(lib_path)
         self._g = _GridHandle(grid)
         self._p = self.params.to_c()
         self._s = _State()
