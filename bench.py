@@ -220,6 +220,8 @@ def main():
     # buffers keep the device footprint of a profiling run to a few GB.
     ap.add_argument("--queue-rays", type=int, default=0)
     ap.add_argument("--deposit-records", type=int, default=0)
+    ap.add_argument("--clock-log-dir", default="/tmp",
+                    help="folder for the nvidia-smi clock samples taken during the timed steps")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -305,8 +307,7 @@ def main():
     torch.cuda.synchronize()
     results = []
     total_ms = 0.0
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    clk = Clocks(os.path.join(args.clock_log_dir, f"clocks_rank{rank}.csv"))
     with clk:
         for _ in range(args.steps):
             flush.zero_()

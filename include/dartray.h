@@ -145,6 +145,9 @@ typedef struct dartray_stats {
                              overflow (the result does not depend on them) */
     double march_sum_ms;  /* with params.profile: sum over ray-march launches of each
                              launch's event span on its stream (march_launches of them) */
+    int64_t flushes;      /* deposit-record flushes (bucketing + per-cell expansion) that ran,
+                             including the one that ends each phase */
+    int64_t batches;      /* source batches traced (both pipelines, restarts excluded) */
 } dartray_stats;
 
 /* Fill *p with the defaults above (r_pre is set when the grid is created if

@@ -88,6 +88,7 @@ struct Pipe {
     float *d_rec_coef = nullptr, *d_srt_coef = nullptr;
     unsigned long long *d_rec_n = nullptr;
     int *d_blocksum = nullptr, *d_total = nullptr;
+    DevStats *d_st = nullptr;  // this pipeline's flush counter (cnt[CT_FLUSH] only)
     // host-side batch bookkeeping
     bool active = false;
     int src_lo = 0, nb = 0;
@@ -132,10 +133,15 @@ struct dartray_grid {
     long long rec_cap = 0;
     cudaEvent_t mev0 = nullptr, mev1 = nullptr;  // around each march launch (profile mode)
     double march_ms = 0.0, flush_ms = 0.0, busy_ms = 0.0, march_sum_ms = 0.0;
-    long long march_launches = 0, restarts = 0;
+    long long march_launches = 0, restarts = 0, batches = 0;
     // peak rays per source of each mode's waves, learned by earlier calls: the
     // first batch of a phase is sized with it (0: not yet known)
     double rays_per_src[3] = {0.0, 0.0, 0.0};
+    // staging buffer for results computed on the device and returned to host
+    // memory (L_abs, maps): allocated on first use, grown on demand, owned by
+    // the grid
+    float *d_stage = nullptr;
+    size_t stage_floats = 0;
 };
 
 namespace {
@@ -144,7 +150,7 @@ void free_all(dartray_grid *g) {
     void *ptrs[] = {g->d_ztab, g->d_node_child, g->d_rope, g->d_node_box, g->d_leaf_box, g->d_dirtab, g->d_kr,
                     g->d_emis, g->d_pxyz, g->d_plum, g->d_U, g->d_ULL, g->d_pend[0], g->d_pend[1], g->d_jtot,
                     g->d_flags, g->d_blocksum, g->d_total, g->d_src_idx, g->d_src_leaf, g->d_src_hint,
-                    g->d_src_pos, g->d_src_S, g->d_st, g->d_sum};
+                    g->d_src_pos, g->d_src_S, g->d_st, g->d_sum, g->d_stage};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kPipes; ++i) {
@@ -152,7 +158,7 @@ void free_all(dartray_grid *g) {
         void *pp[] = {P.d_pd, P.d_H[0], P.d_H[1], P.d_M[0], P.d_M[1], P.d_L, P.d_HI[0], P.d_HI[1], P.d_MI[0],
                       P.d_MI[1], P.d_LI, P.d_hkey, P.d_hcnt, P.d_hmem, P.d_rec_cell, P.d_cnt,
                       P.d_off, P.d_cur, P.d_rec_dir, P.d_srt_dir, P.d_rec_coef, P.d_srt_coef, P.d_rec_n,
-                      P.d_blocksum, P.d_total};
+                      P.d_blocksum, P.d_total, P.d_st};
         for (void *p : pp)
             if (p) cudaFree(p);
         if (P.h_pd) cudaFreeHost(P.h_pd);
@@ -247,7 +253,7 @@ int enqueue_flush_kernels(dartray_grid *g, Pipe &P, float *pend_dst, int force) 
     cudaStream_t s = P.stream;
     const int nb = (g->n_leaf + kBlock - 1) / kBlock;
     const unsigned gb = static_cast<unsigned>(8 * g->num_sms);
-    flush_decide_kernel<<<1, 1, 0, s>>>(P.d_pd, P.d_rec_n, g->rec_cap, force);
+    flush_decide_kernel<<<1, 1, 0, s>>>(P.d_pd, P.d_rec_n, g->rec_cap, force, P.d_st);
     scan_blocks_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, reinterpret_cast<const int *>(P.d_cnt), g->n_leaf, P.d_blocksum);
     scan_offsets_kernel<<<1, 1, 0, s>>>(P.d_pd, P.d_blocksum, nb, P.d_total);
     scan_apply_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, P.d_cnt, g->n_leaf, P.d_blocksum, P.d_off, P.d_cur);
@@ -455,6 +461,7 @@ struct PhaseResult {
     unsigned long long cnt[CT_N];
     double f_u;
     double pend_sum;
+    long long batches;
 };
 
 int status_error(const PipeDev &h, int mode) {
@@ -546,6 +553,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
         for (int i = 0; i < kPipes; ++i) {
             Pipe &P = g->pipe[i];
             P.active = false;
+            CK(cudaMemsetAsync(P.d_st, 0, sizeof(DevStats), s));
             if (g->rec_cap > 0) {
                 CK(cudaMemsetAsync(P.d_rec_n, 0, sizeof(unsigned long long), s));
                 CK(cudaMemsetAsync(P.d_cnt, 0, static_cast<size_t>(g->n_leaf) * sizeof(unsigned), s));
@@ -565,6 +573,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
         bool overflow = false;
         long long failed_nb = 0;
         long long next = 0;
+        long long batches = 0;
         // Each pipeline runs kWavesAhead waves per host round trip.  The host
         // refills whichever pipeline finishes its waves first, so neither
         // waits for the other.
@@ -583,6 +592,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
                     const int nb = static_cast<int>(std::min<long long>(want, n_src - next));
                     if ((rc = start_batch(g, P, static_cast<int>(next), nb, kstart))) return rc;
                     next += nb;
+                    ++batches;
                 }
                 if (P.active) {
                     any = true;
@@ -647,10 +657,17 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
             CK(cudaStreamSynchronize(s));
             out.cnt[CT_WAVES] += static_cast<unsigned long long>(waves);
             out.cnt[CT_SOURCES] += static_cast<unsigned long long>(n_src);
+            for (int i = 0; i < kPipes; ++i) {
+                DevStats ps{};
+                CK(cudaMemcpyAsync(&ps, g->pipe[i].d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                out.cnt[CT_FLUSH] += ps.cnt[CT_FLUSH];
+            }
             CK(cudaMemcpyAsync(g->d_st, &out, sizeof(DevStats), cudaMemcpyHostToDevice, s));
             std::memcpy(res->ledger, out.ledger, sizeof res->ledger);
             std::memcpy(res->cnt, out.cnt, sizeof res->cnt);
             g->rays_per_src[mode] = std::max(rps_floor, max_rps);
+            g->batches += batches;
             break;
         }
         ++g->restarts;
@@ -687,6 +704,7 @@ void fill_stats(const dartray_grid *g, const PhaseResult &r, dartray_stats *st) 
     st->waves = r.cnt[CT_WAVES];
     st->sources = r.cnt[CT_SOURCES];
     st->jsca_pixels = r.cnt[CT_JPIX];
+    st->flushes = r.cnt[CT_FLUSH];
     for (int l = 0; l < g->nl; ++l) {
         const double w = g->G.albedo[l];
         st->emitted[l] = r.ledger[LG_EMITTED][l];
@@ -704,6 +722,22 @@ void fill_stats(const dartray_grid *g, const PhaseResult &r, dartray_stats *st) 
 
 int set_device(dartray_grid *g) {
     CK(cudaSetDevice(g->device));
+    return DARTRAY_OK;
+}
+
+// The grid's staging buffer with room for n floats.
+int stage_buffer(dartray_grid *g, size_t n, float **out) {
+    if (g->stage_floats < n) {
+        if (g->d_stage) {
+            CK(cudaStreamSynchronize(g->stream));
+            CK(cudaFree(g->d_stage));
+            g->d_stage = nullptr;
+            g->stage_floats = 0;
+        }
+        CK(cudaMalloc(reinterpret_cast<void **>(&g->d_stage), n * sizeof(float)));
+        g->stage_floats = n;
+    }
+    *out = g->d_stage;
     return DARTRAY_OK;
 }
 
@@ -860,6 +894,7 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
         AL(P.d_hcnt, g->hcap);
         AL(P.d_hmem, g->hcap);
         AL(P.d_pd, 1);
+        AL(P.d_st, 1);
         if (g->rec_cap > 0) {
             AL(P.d_rec_cell, g->rec_cap);
             AL(P.d_rec_dir, g->rec_cap);
@@ -879,7 +914,8 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
             cudaStreamCreateWithFlags(&P.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&P.ev, cudaEventDisableTiming) != cudaSuccess)
             return bail(fail(DARTRAY_E_CUDA, "pipeline stream setup failed"));
-        if (cudaMemsetAsync(P.d_pd, 0, sizeof(PipeDev), g->stream) != cudaSuccess)
+        if (cudaMemsetAsync(P.d_pd, 0, sizeof(PipeDev), g->stream) != cudaSuccess ||
+            cudaMemsetAsync(P.d_st, 0, sizeof(DevStats), g->stream) != cudaSuccess)
             return bail(fail(DARTRAY_E_CUDA, "memset failed"));
     }
 #undef AL
@@ -966,7 +1002,7 @@ int dartray_direct(dartray_grid *g, dartray_stats *stats) {
     g->cur = 0;  // step 2 deposits into d_pend[1]
     const long long l0 = g->launches;
     g->march_ms = g->flush_ms = g->busy_ms = g->march_sum_ms = 0.0;
-    g->march_launches = g->restarts = 0;
+    g->march_launches = g->restarts = g->batches = 0;
     CK(cudaEventRecord(g->ev0, g->stream));
     PhaseResult r1{}, r2{};
     if ((rc = run_phase(g, MODE_LL, &r1))) return rc;
@@ -987,6 +1023,7 @@ int dartray_direct(dartray_grid *g, dartray_stats *stats) {
         stats->busy_ms = g->busy_ms;
         stats->restarts = g->restarts;
         stats->march_sum_ms = g->march_sum_ms;
+        stats->batches = g->batches;
     }
     return DARTRAY_OK;
 }
@@ -1000,7 +1037,7 @@ int dartray_scatter_iter(dartray_grid *g, double *remaining_frac, dartray_stats 
     CK(cudaMemsetAsync(g->d_st, 0, sizeof(DevStats), g->stream));
     const long long l0 = g->launches;
     g->march_ms = g->flush_ms = g->busy_ms = g->march_sum_ms = 0.0;
-    g->march_launches = g->restarts = 0;
+    g->march_launches = g->restarts = g->batches = 0;
     CK(cudaEventRecord(g->ev0, g->stream));
     PhaseResult r{};
     if ((rc = run_phase(g, MODE_SCATTER, &r))) return rc;
@@ -1019,6 +1056,7 @@ int dartray_scatter_iter(dartray_grid *g, double *remaining_frac, dartray_stats 
         stats->busy_ms = g->busy_ms;
         stats->restarts = g->restarts;
         stats->march_sum_ms = g->march_sum_ms;
+        stats->batches = g->batches;
     }
     return DARTRAY_OK;
 }
@@ -1033,16 +1071,12 @@ int dartray_rfed(dartray_grid *g, float *U, float *L_abs, int dst_is_device) {
     if (U) CK(cudaMemcpyAsync(U, g->d_U, nU * sizeof(float), k, g->stream));
     if (L_abs) {
         float *dst = L_abs;
-        if (!dst_is_device) CK(cudaMalloc(reinterpret_cast<void **>(&dst), nU * sizeof(float)));
+        if (!dst_is_device && (rc = stage_buffer(g, nU, &dst))) return rc;
         labs_kernel<<<static_cast<unsigned>((nU + kBlock - 1) / kBlock), kBlock, 0, g->stream>>>(
             g->G, g->d_U, static_cast<float>(g->P.c_light), dst);
         ++g->launches;
         CK(cudaGetLastError());
-        if (!dst_is_device) {
-            CK(cudaMemcpyAsync(L_abs, dst, nU * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
-            CK(cudaStreamSynchronize(g->stream));
-            cudaFree(dst);
-        }
+        if (!dst_is_device) CK(cudaMemcpyAsync(L_abs, dst, nU * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
     }
     CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
@@ -1080,7 +1114,7 @@ int dartray_map(dartray_grid *g, const double observer[3], int32_t nside_k, int3
     const long long npix = 12ll << (2 * nside_k);
     const size_t nmap = static_cast<size_t>(npix) * g->nl;
     float *dst = map;
-    if (!dst_is_device) CK(cudaMalloc(reinterpret_cast<void **>(&dst), nmap * sizeof(float)));
+    if (!dst_is_device && (rc = stage_buffer(g, nmap, &dst))) return rc;
     CK(cudaMemsetAsync(dst, 0, nmap * sizeof(float), g->stream));
     MapArgs M{};
     for (int a = 0; a < 3; ++a) M.obs[a] = observer[a];  // double: exact subdivision / pixel decisions
@@ -1093,11 +1127,7 @@ int dartray_map(dartray_grid *g, const double observer[3], int32_t nside_k, int3
     if (rc) return fail(DARTRAY_E_INVAL, "unsupported n_lambda for maps");
     ++g->launches;
     CK(cudaGetLastError());
-    if (!dst_is_device) {
-        CK(cudaMemcpyAsync(map, dst, nmap * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
-        CK(cudaStreamSynchronize(g->stream));
-        cudaFree(dst);
-    }
+    if (!dst_is_device) CK(cudaMemcpyAsync(map, dst, nmap * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
 }

@@ -326,7 +326,7 @@ __device__ __host__ inline unsigned rr_meta(int lev, int kind, int axis) {
 // ledger slots (luminosities) and counters
 enum { LG_EMITTED = 0, LG_DEPOSITED, LG_ESCAPED, LG_BLOCKED, LG_CUT, LG_SKIPPED, LG_N };
 enum { CT_RAYS = 0, CT_CROSS, CT_SPLIT, CT_MERGE, CT_BLOCK, CT_ESCAPE, CT_CUT, CT_LOW, CT_RESUME,
-       CT_WAVES, CT_SOURCES, CT_JPIX, CT_N };
+       CT_WAVES, CT_SOURCES, CT_JPIX, CT_FLUSH, CT_N };
 
 struct DevStats {
     double ledger[LG_N][kMaxLambda];

@@ -1052,10 +1052,12 @@ __global__ void scan_apply_kernel(const PipeDev *pd, const unsigned *cnt, int n,
 // The flush runs when the pipeline's record buffer is half full (or when the
 // host forces it); every flush kernel reads the decision and the record count
 // from device memory.
-__global__ void flush_decide_kernel(PipeDev *pd, const unsigned long long *rec_n, long long rec_cap, int force) {
+__global__ void flush_decide_kernel(PipeDev *pd, const unsigned long long *rec_n, long long rec_cap, int force,
+                                    DevStats *st) {
     const unsigned long long n = *rec_n;
     if (n > pd->peak_rec) pd->peak_rec = n;
     pd->flush = (n > 0 && (force || static_cast<long long>(n) >= rec_cap / 2)) ? 1 : 0;
+    if (pd->flush) st->cnt[CT_FLUSH] += 1;  // single thread; the pipelines' stats words differ
 }
 
 __global__ void flush_reset_kernel(PipeDev *pd, unsigned long long *rec_n, unsigned *cnt, int n_leaf) {

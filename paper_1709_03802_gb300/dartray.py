@@ -56,7 +56,8 @@ class dartray_stats(C.Structure):
                [("f_u", C.c_double), ("l_sca2", C.c_double), ("gpu_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("march_ms", C.c_double), ("march_launches", C.c_int64),
                 ("jsca_pixels", C.c_int64), ("flush_ms", C.c_double), ("busy_ms", C.c_double),
-               ("restarts", C.c_int64), ("march_sum_ms", C.c_double)]
+               ("restarts", C.c_int64), ("march_sum_ms", C.c_double), ("flushes", C.c_int64),
+               ("batches", C.c_int64)]
 
     def to_dict(self, n_lambda=1):
         out = {}
@@ -270,11 +271,13 @@ class DartRay:
             pass
 
     def direct(self):
-        return dartray_direct(self._h).to_dict(self.n_lambda)
+        self.last_stats = dartray_direct(self._h).to_dict(self.n_lambda)
+        return self.last_stats
 
     def scatter_iter(self):
         rem, st = dartray_scatter_iter(self._h)
-        return rem, st.to_dict(self.n_lambda)
+        self.last_stats = st.to_dict(self.n_lambda)
+        return rem, self.last_stats
 
     def rfed(self, U=None, L_abs=None):
         dev = _is_cuda_tensor(U) or _is_cuda_tensor(L_abs)
