@@ -81,6 +81,7 @@ typedef struct {
     int32_t max_cross;  /* crossing cap per ray (error if hit) */
     int32_t max_waves;  /* wave cap per source (error if hit) */
     int32_t src_stride, src_offset; /* process sources with index % stride == offset */
+    int32_t octant;     /* 1: octant mode of Sect. 3.6.4 (symmetric models) */
 } or_params;
 
 /* ledger slots per wavelength */
@@ -418,6 +419,7 @@ typedef struct {
     /* j_sca pixel directions per wavelength level */
     double *pixdir[4];
     int nl;
+    double wsrc;              /* octant mode: weight of the current source, else 1 */
 } or_ctx;
 
 /* Per-crossing deposit quantities (paper Sect. 2, Sect. 3.5; reading of the
@@ -441,6 +443,9 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
     double n[3];
     or_pix2vec(ray->lev, ray->pix, n);
     const double omega_k = 4.0 * OR_PI / (12.0 * ldexp(1.0, 2 * ray->lev));
+    /* the ray's beam solid angle carries the source weight (octant mode):
+     * deposits and ledger entries scale with it, the tests below do not */
+    const double omega_w = omega_k * C->wsrc;
     /* Eq. 2 / Eq. 3 compared as  4 pi N r^2  vs  12 4^k L^2  (both sides exact
      * or singly rounded; Omega_INT = L^2/r^2, reading). */
     const double split_c = 4.0 * OR_PI * (double)P->n_rays_min;
@@ -493,7 +498,7 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
         }
     }
     if (leaf < 0) {  /* starts outside the model */
-        for (int l = 0; l < nl; ++l) S->ledger[l][LG_ESCAPED] += ray->I[l] * omega_k;
+        for (int l = 0; l < nl; ++l) S->ledger[l][LG_ESCAPED] += ray->I[l] * omega_w;
         S->counters[CT_ESCAPE]++;
         return 0;
     }
@@ -515,7 +520,7 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
                           (xc[1] - C->xs[1]) * (xc[1] - C->xs[1]) +
                           (xc[2] - C->xs[2]) * (xc[2] - C->xs[2]);
         const int in_src = (leaf == C->src_leaf);
-        const double P_in_unit = omega_k;  /* beam solid angle */
+        const double P_in_unit = omega_w;  /* beam solid angle (times the source weight) */
         int neg[OR_MAXL] = {0};
         double fac[OR_MAXL], T[OR_MAXL];
         for (int l = 0; l < nl; ++l) {
@@ -527,7 +532,7 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
             if (C->mode == 0) {
                 /* step 1: the significance test is d_ray < R_pre (Fig. 1) */
                 if (d >= P->r_pre) {
-                    for (int l = 0; l < nl; ++l) S->ledger[l][LG_CUT] += ray->I[l] * omega_k;
+                    for (int l = 0; l < nl; ++l) S->ledger[l][LG_CUT] += ray->I[l] * omega_w;
                     S->counters[CT_CUT]++;
                     return 0;
                 }
@@ -544,7 +549,7 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
                     all &= neg[l];
                 }
                 if (all) {
-                    for (int l = 0; l < nl; ++l) S->ledger[l][LG_BLOCKED] += ray->I[l] * omega_k;
+                    for (int l = 0; l < nl; ++l) S->ledger[l][LG_BLOCKED] += ray->I[l] * omega_w;
                     S->counters[CT_BLOCK]++;
                     return 0;
                 }
@@ -616,7 +621,7 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
         leaf = or_locate(G, pe, n, box);
         if (leaf == prev) return -5;  /* no progress: inexact face coordinates */
         if (leaf < 0) {
-            for (int l = 0; l < nl; ++l) S->ledger[l][LG_ESCAPED] += ray->I[l] * omega_k;
+            for (int l = 0; l < nl; ++l) S->ledger[l][LG_ESCAPED] += ray->I[l] * omega_w;
             S->counters[CT_ESCAPE]++;
             return 0;
         }
@@ -744,6 +749,45 @@ static void or_leaf_boxes(const or_grid *G, double *out) {
     free(sb);
 }
 
+/* Octant mode (Sect. 3.6.4): a model symmetric under the reflections about
+ * the planes through the centre of its root lattice is traced from the
+ * sources of the first octant only; the field of a source's image is the
+ * image of the source's field, so every cell receives the deposits of the
+ * images of itself.  mirror[(m-1) n_leaf + c] is the image of leaf c under
+ * reflection mask m (bit a: axis a flipped), mpix[m-1][k][q] the image of
+ * pixel q of level k.  Returns -6 if the grid is not symmetric. */
+static int or_mirrors(const or_grid *G, const double *leaf_box, const double centre[3], int32_t *mirror,
+                      int32_t mpix[7][4][768]) {
+    for (int m = 1; m < 8; ++m) {
+        for (int64_t c = 0; c < G->n_leaf; ++c) {
+            const double *b = leaf_box + 4 * c;
+            double q[3];
+            for (int a = 0; a < 3; ++a) {
+                const double mid = b[a] + 0.5 * b[3];
+                q[a] = ((m >> a) & 1) ? 2.0 * centre[a] - mid : mid;
+            }
+            const double up[3] = {1, 1, 1};
+            double box[4];
+            const int img = or_locate(G, q, up, box);
+            if (img < 0 || box[3] != b[3]) return -6;
+            for (int l = 0; l < G->n_lambda; ++l)
+                if (G->kappa_rho[c * G->n_lambda + l] != G->kappa_rho[(int64_t)img * G->n_lambda + l] ||
+                    G->emis[c * G->n_lambda + l] != G->emis[(int64_t)img * G->n_lambda + l])
+                    return -6;
+            mirror[(int64_t)(m - 1) * G->n_leaf + c] = img;
+        }
+        for (int k = 0; k < 4; ++k)
+            for (int q = 0; q < (12 << (2 * k)); ++q) {
+                double v[3];
+                or_pix2vec(k, q, v);
+                for (int a = 0; a < 3; ++a)
+                    if ((m >> a) & 1) v[a] = -v[a];
+                mpix[m - 1][k][q] = (int32_t)or_vec2pix(k, v);
+            }
+    }
+    return 0;
+}
+
 /* One phase of the sweep: mode 0 = step 1 (U_LL), 1 = step 2 (direct light),
  * 2 = one scattering iteration.  Returns 0 or a negative error. */
 static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode) {
@@ -786,6 +830,10 @@ static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode)
      * steps 1-2, cells holding scattered luminosity for an iteration) */
     const int64_t nsrc_all = mode == 2 ? G->n_leaf : (int64_t)G->n_leaf + G->n_point;
     char *is_src = (char *)calloc((size_t)nsrc_all, 1);
+    double *leaf_box = (double *)malloc(sizeof(double) * 4 * (size_t)G->n_leaf);
+    or_leaf_boxes(G, leaf_box);
+    double centre[3];
+    for (int a = 0; a < 3; ++a) centre[a] = G->root_lo[a] + 0.5 * G->nroot[a] * G->root_size;
     int64_t ns = 0;
     for (int64_t s = 0; s < nsrc_all; ++s) {
         int on = 0;
@@ -802,13 +850,43 @@ static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode)
         } else {
             for (int l = 0; l < nl; ++l) on |= G->point_lum[(s - G->n_leaf) * nl + l] > 0;
         }
-        if (on && (s % P->src_stride) == P->src_offset) { is_src[s] = 1; ++ns; }
+        if (on && (s % P->src_stride) == P->src_offset) {
+            ++ns;  /* N_s counts every source of the model */
+            if (P->octant) {
+                /* octant mode: sources of the first octant (closed) only */
+                double x[3];
+                for (int a = 0; a < 3; ++a)
+                    x[a] = s < G->n_leaf ? leaf_box[4 * s + a] + 0.5 * leaf_box[4 * s + 3]
+                                         : G->point_xyz[3 * (s - G->n_leaf) + a];
+                on = x[0] >= centre[0] && x[1] >= centre[1] && x[2] >= centre[2];
+            }
+            is_src[s] = (char)on;
+        }
     }
     S->n_src = (int32_t)ns;
     C.f_u = ns > 0 ? 4.0 * P->a_rt / (double)ns : 0.0;  /* Eq. 10 */
     S->f_u = C.f_u;
-    double *leaf_box = (double *)malloc(sizeof(double) * 4 * (size_t)G->n_leaf);
-    or_leaf_boxes(G, leaf_box);
+    /* octant mode: deposits of the traced sources go to scratch arrays and
+     * are folded over the eight images of every cell at the end */
+    double *dep_U = NULL, *dep_P = NULL, *final_target = C.target, *final_pend = C.pend_dst;
+    int32_t *mirror = NULL;
+    static int32_t mpix[7][4][768];
+    if (P->octant) {
+        mirror = (int32_t *)malloc(sizeof(int32_t) * 7 * (size_t)G->n_leaf);
+        if (or_mirrors(G, leaf_box, centre, mirror, mpix)) {
+            free(mirror);
+            free(is_src);
+            free(leaf_box);
+            for (int k = 0; k < 4; ++k) free(C.pixdir[k]);
+            return -6;
+        }
+        dep_U = (double *)calloc((size_t)G->n_leaf * nl, sizeof(double));
+        C.target = dep_U;
+        if (mode != 0) {
+            dep_P = (double *)calloc((size_t)S->sca_len, sizeof(double));
+            C.pend_dst = dep_P;
+        }
+    }
     int rc = 0;
     or_list wave = {0};
     const double omega0 = 4.0 * OR_PI / (12.0 * ldexp(1.0, 2 * kstart));
@@ -816,6 +894,18 @@ static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode)
         if (!is_src[s]) continue;
         S->counters[CT_SOURCES]++;
         double box[4];
+        {
+            /* weight 1/2^k of a source on k mirror planes (it is its own image
+             * under 2^k of the eight reflections); 1 outside the octant mode */
+            double x[3];
+            for (int a = 0; a < 3; ++a)
+                x[a] = s < G->n_leaf ? leaf_box[4 * s + a] + 0.5 * leaf_box[4 * s + 3]
+                                     : G->point_xyz[3 * (s - G->n_leaf) + a];
+            int k = 0;
+            if (P->octant)
+                for (int a = 0; a < 3; ++a) k += x[a] == centre[a];
+            C.wsrc = ldexp(1.0, -k);
+        }
         if (s < G->n_leaf) {
             memcpy(box, leaf_box + 4 * s, sizeof box);
             C.xs[0] = box[0] + 0.5 * box[3];
@@ -858,7 +948,7 @@ static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode)
                     Il = G->point_lum[(s - G->n_leaf) * nl + l] / (4.0 * OR_PI);
                 }
                 r.I[l] = Il;
-                S->ledger[l][LG_EMITTED] += Il * omega0;
+                S->ledger[l][LG_EMITTED] += Il * omega0 * C.wsrc;
             }
             if (or_push(&wave, &r)) { rc = -1; break; }
         }
@@ -868,6 +958,36 @@ static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode)
     free(is_src);
     free(leaf_box);
     for (int k = 0; k < 4; ++k) free(C.pixdir[k]);
+    if (P->octant) {
+        if (!rc) {
+            /* fold: every cell (and j_sca pixel) receives the deposits of its
+             * images; the ledger describes the whole model */
+            for (int64_t c = 0; c < G->n_leaf; ++c)
+                for (int l = 0; l < nl; ++l) {
+                    double v = dep_U[c * nl + l];
+                    for (int m = 1; m < 8; ++m) v += dep_U[(int64_t)mirror[(int64_t)(m - 1) * G->n_leaf + c] * nl + l];
+                    final_target[c * nl + l] += v;
+                }
+            if (mode != 0)
+                for (int l = 0; l < nl; ++l) {
+                    const int kl = S->k_lam[l], npx = 12 << (2 * kl);
+                    for (int64_t c = 0; c < G->n_leaf; ++c)
+                        for (int q = 0; q < npx; ++q) {
+                            double v = dep_P[S->off_lam[l] + c * npx + q];
+                            for (int m = 1; m < 8; ++m) {
+                                const int64_t cm = mirror[(int64_t)(m - 1) * G->n_leaf + c];
+                                v += dep_P[S->off_lam[l] + cm * npx + mpix[m - 1][kl][q]];
+                            }
+                            final_pend[S->off_lam[l] + c * npx + q] = v;
+                        }
+                }
+            for (int l = 0; l < nl; ++l)
+                for (int i = 0; i < LG_N; ++i) S->ledger[l][i] *= 8.0;
+        }
+        free(dep_U);
+        free(dep_P);
+        free(mirror);
+    }
     if (rc) return rc;
     if (mode >= 1) {
         double tot = 0;

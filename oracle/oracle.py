@@ -77,7 +77,8 @@ class _Params(C.Structure):
                 ("c_light", C.c_double), ("n_rays_min", C.c_int32), ("n_rays_max", C.c_int32),
                 ("k0", C.c_int32), ("k_ray_max", C.c_int32), ("k_sca_cap", C.c_int32),
                 ("n_fwhm", C.c_int32), ("merge", C.c_int32), ("max_cross", C.c_int32),
-                ("max_waves", C.c_int32), ("src_stride", C.c_int32), ("src_offset", C.c_int32)]
+                ("max_waves", C.c_int32), ("src_stride", C.c_int32), ("src_offset", C.c_int32),
+                ("octant", C.c_int32)]
 
 
 class _State(C.Structure):
@@ -251,6 +252,7 @@ class OracleParams:
     max_waves: int = 200
     src_stride: int = 1
     src_offset: int = 0
+    octant: int = 0
 
     def to_c(self):
         p = _Params()
@@ -264,7 +266,8 @@ class OracleError(RuntimeError):
 
 
 _ERRORS = {-1: "out of memory", -2: "crossing cap reached", -3: "wave cap reached",
-           -4: "source cell not found", -5: "no progress across a face (inexact grid coordinates)"}
+           -4: "source cell not found", -5: "no progress across a face (inexact grid coordinates)",
+           -6: "octant mode: the model is not mirror-symmetric about its centre"}
 
 
 class Oracle:
