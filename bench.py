@@ -59,6 +59,10 @@ def bytes_per_crossing(nl):
     return 44 + 16 * nl
 
 
+# a deposit record: cell (4 B) and the ray direction with the HG coefficient (16 B)
+RECORD_BYTES = 20
+
+
 def make_workload():
     import synth
     grid = synth.config2()
@@ -138,6 +142,7 @@ def run_step(gpu, grid):
     flush_ms = st["flush_ms"]
     march_cross = st["crossings"]
     jpix = st["jsca_pixels"]
+    records = st["records"]
     launches = st["kernel_launches"]
     it_ms = []
     it = 0
@@ -151,6 +156,7 @@ def run_step(gpu, grid):
         flush_ms += s2["flush_ms"]
         march_cross += s2["crossings"]
         jpix += s2["jsca_pixels"]
+        records += s2["records"]
         launches += s2["kernel_launches"]
         it_ms.append(s2["gpu_ms"])
         if rem < F_L:
@@ -158,7 +164,7 @@ def run_step(gpu, grid):
     m = gpu.map(OBSERVER, MAP_K, max_sub=MAP_SUB, use_jsca=True)
     launches += 1
     return dict(crossings=cross, march_ms=march_ms, march_sum_ms=march_sum_ms, march_launches=march_launches,
-                flush_ms=flush_ms, march_crossings=march_cross, jsca_pixels=jpix,
+                flush_ms=flush_ms, march_crossings=march_cross, jsca_pixels=jpix, records=records,
                 iters=it, iter_ms=it_ms, launches=launches, map=m)
 
 
@@ -332,8 +338,7 @@ def main():
     # algorithmic bytes of the marcher: per crossing (leaf box, face link, node
     # word, kappa*rho, U_LL, U read-modify-write) plus one 24-byte deposit
     # record per depositing crossing (j_sca pixels / pixels per row)
-    npx = 12 * 4 ** gpu.k_lam[0]
-    alg_bytes = sum(r["march_crossings"] * bytes_per_crossing(nl) + 24 * r["jsca_pixels"] / npx for r in results)
+    alg_bytes = sum(r["march_crossings"] * bytes_per_crossing(nl) + RECORD_BYTES * r["records"] for r in results)
     peak, peak_src = peaks()
     # per launch: algorithmic bytes / the launch's CUDA-event span on its
     # stream, averaged over the launches (= all bytes / summed spans; a span
@@ -365,6 +370,7 @@ def main():
                 "s_per_scatter_iter": float(np.mean(it_ms)) / 1e3 if it_ms else None,
                 "scatter_iters_per_step": float(np.mean([r["iters"] for r in results])),
                 "crossings_per_step": cross,
+                "deposit_records_per_step": float(np.mean([r["records"] for r in results])),
                 "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
                 "gpu_launches": int(sum(r["launches"] for r in results)), "clocks": clocks}
         print(json.dumps(line))

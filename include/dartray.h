@@ -115,6 +115,18 @@ typedef struct dartray_params {
                                per-cell accumulation of crossing records, atomics only
                                when the record buffer is full) */
     int64_t deposit_records; /* record buffer capacity; 0 = automatic (0) */
+    int32_t deterministic;   /* 1: bit-identical results from run to run: U, the j_sca rows
+                                and the ledger are summed in 64-bit fixed point (exponents
+                                from bounds of each cell's total), so no sum depends on the
+                                order of the GPU's additions; slower deposits (0) */
+    int32_t octant;          /* 1: octant mode for models symmetric under the reflections about
+                                the planes through the centre of the root lattice (axisymmetric
+                                models with a symmetric vertical profile; Sect. 3.6.4): only
+                                sources in the first octant are traced and each deposit is
+                                also made, reflected, in the other seven octants.  Same result
+                                as the full mode; counters count the rays traced.  Requires
+                                src_stride 1; a grid that is not symmetric is rejected with
+                                DARTRAY_E_INVAL (0) */
 } dartray_params;
 
 /* Per-call statistics.  Ledger entries are luminosities per wavelength of the
@@ -148,6 +160,8 @@ typedef struct dartray_stats {
     int64_t flushes;      /* deposit-record flushes (bucketing + per-cell expansion) that ran,
                              including the one that ends each phase */
     int64_t batches;      /* source batches traced (both pipelines, restarts excluded) */
+    int64_t records;      /* j_sca deposit records written by the ray marcher (one per
+                             depositing crossing of steps 2-3 not deposited directly) */
 } dartray_stats;
 
 /* Fill *p with the defaults above (r_pre is set when the grid is created if
@@ -165,6 +179,37 @@ int dartray_params_default(dartray_params *p);
  */
 int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *params,
                         void *cuda_stream, dartray_grid **out);
+
+/*
+ * Several independent models in one grid, traced together: every wave of
+ * the ray marcher holds rays of all models, so many small models fill the
+ * GPU as one large model does (the paper's method is additive over sources,
+ * and no ray leaves its model).  descs[m] describes model m as for
+ * dartray_grid_create; all models share n_lambda, albedo and g (one dust
+ * model).  Leaves and point sources are numbered model after model (see
+ * dartray_model_info); dartray_rfed and dartray_jsca return all models
+ * concatenated that way.  Each model keeps its own N_s (Eq. 10) and R_pre
+ * (0.15 of its size when params->r_pre < 0).  dartray_scatter_iter stops a
+ * model's emission once its remaining fraction is below params->f_l (as a
+ * loop over single-model grids would stop it) and returns the largest
+ * remaining fraction.  Not supported on batched grids: the octant mode,
+ * maps, state files.  n_models <= 4096 / (6 n_lambda).  Errors as
+ * dartray_grid_create.
+ */
+int dartray_grid_create_batch(const dartray_grid_desc *descs, int32_t n_models, const dartray_params *params,
+                              void *cuda_stream, dartray_grid **out);
+
+/* Layout and state of model `model` of a grid (a single-model grid has
+ * model 0): first leaf and number of leaves, first point source, remaining
+ * scattered fraction after the last call, 1 while it still emits in
+ * scattering iterations.  Any pointer may be NULL.  Errors: INVAL. */
+int dartray_model_info(const dartray_grid *grid, int32_t model, int64_t *leaf_offset, int32_t *n_leaf,
+                       int64_t *point_offset, double *remaining_frac, int32_t *active);
+
+/* Ledger of model `model` for the last phase of the last call, its f_U and
+ * its scattered luminosity at the end of step 2 (other fields 0).  Errors:
+ * INVAL. */
+int dartray_model_stats(const dartray_grid *grid, int32_t model, dartray_stats *stats);
 
 /* Steps 1 and 2 of Sect. 2: U_LL within R_pre, then direct light with ray
  * blocking (Eq. 1), depositing U, and the scattered luminosity into the

@@ -1,7 +1,8 @@
 """Build of libdartray.so (CUDA, sm_103a) in-tree.
 
-One nvcc invocation compiles the two translation units (the CUDA sweep and
-the host grid builder) into paper_1709_03802_gb300/_build/libdartray.so.
+The translation units (the CUDA sweep, the marcher for 4-16 wavelengths and
+the host grid builder) compile in parallel and link into
+paper_1709_03802_gb300/_build/libdartray.so.
 """
 import os
 import subprocess
@@ -11,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdartray.so")
-SOURCES = [os.path.join(CSRC, "dartray.cu"), os.path.join(CSRC, "grid_host.cpp")]
+SOURCES = [os.path.join(CSRC, "dartray.cu"), os.path.join(CSRC, "march_wide.cu"), os.path.join(CSRC, "grid_host.cpp")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + \
     [os.path.join(os.path.dirname(HERE), "include", "dartray.h")]
 
@@ -28,12 +29,24 @@ def build(force=False, verbose=False):
         if os.path.getmtime(LIB) >= newest:
             return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
-           "-Xcompiler", "-fPIC", "-shared", "-o", tmp] + SOURCES
+    flags = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
+        flags.append("-Xptxas=-v")
+    # translation units in parallel, then one link
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(BUILD, os.path.basename(src) + f".{os.getpid()}.o")
+        cmd = [nvcc()] + flags + ["-c", src, "-o", obj]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append(subprocess.Popen(cmd))
+        objs.append(obj)
+    bad = [p.args for p in procs if p.wait() != 0]
+    if bad:
+        raise subprocess.CalledProcessError(1, bad[0])
+    subprocess.check_call([nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp] + objs)
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

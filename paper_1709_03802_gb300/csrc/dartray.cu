@@ -19,6 +19,7 @@
 #include "../../include/dartray.h"
 #include "grid_host.h"
 #include "map_kernels.cuh"
+#include "march_wide.h"
 #include "sweep_kernels.cuh"
 
 using namespace dartray;
@@ -65,6 +66,7 @@ int k_hp_host(double g, int n_fwhm, int cap) {
 }  // namespace
 
 constexpr int kPipes = 2;
+constexpr int kMaxModels = 4096;
 
 // Map staging buffer of dartray_map_noalloc: a fixed device array (8 MiB), so
 // that entry point needs no allocation.  Every device that loads the library
@@ -82,7 +84,8 @@ struct Pipe {
     unsigned long long *d_hkey = nullptr;
     int *d_hcnt = nullptr;
     int4 *d_hmem = nullptr;
-    // deferred deposit records
+    // deferred deposit records (cell, ray direction, HG coefficients) and
+    // their copy in cell order
     unsigned *d_rec_cell = nullptr, *d_cnt = nullptr, *d_off = nullptr, *d_cur = nullptr;
     float4 *d_rec_dir = nullptr, *d_srt_dir = nullptr;
     float *d_rec_coef = nullptr, *d_srt_coef = nullptr;
@@ -128,7 +131,7 @@ struct dartray_grid {
     long long launches = 0;
     int num_sms = 1;
     int march_blocks = 1;
-    int acc_blocks[4] = {1, 1, 1, 1};  // resident blocks of cell_accumulate_kernel<1, 2, 6, 24>
+    int acc_blocks[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // resident blocks of cell_accumulate_kernel<1, 2, 6, 24> (x2: det)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long rec_cap = 0;
     cudaEvent_t mev0 = nullptr, mev1 = nullptr;  // around each march launch (profile mode)
@@ -142,6 +145,31 @@ struct dartray_grid {
     // the grid
     float *d_stage = nullptr;
     size_t stage_floats = 0;
+    // deterministic mode: fixed-point sums of U and of the pending j_sca of
+    // the running phase, with per-wavelength exponents (see to_fix)
+    unsigned long long *d_Ufix = nullptr, *d_pfix = nullptr;
+    int32_t *d_mirror = nullptr, *d_mirror_pix = nullptr;  // octant mode
+    float *d_oct_u = nullptr, *d_oct_p = nullptr;           // octant mode: deposits of the traced sources
+    float *d_thr = nullptr;       // [n_leaf][nl] Eq. 1 thresholds f_U U_LL of the running phase
+    float *d_fu_model = nullptr;  // [n_models] f_U of the running phase
+    // batched grids (several models in one forest)
+    int n_models = 1;
+    ModelDev *d_models = nullptr;
+    uint16_t *d_leaf_model = nullptr, *d_point_model = nullptr;
+    unsigned char *d_model_active = nullptr;
+    int *d_mcount = nullptr;
+    double *d_mled = nullptr;
+    unsigned long long *d_mled_fix = nullptr;
+    long long *d_seg_beg = nullptr, *d_seg_len = nullptr;  // (model, wavelength) blocks of the j_sca array
+    double *d_seg_out = nullptr;
+    int march_smem = 0;
+    std::vector<long long> m_leaf0, m_point0;
+    std::vector<int> m_nleaf;
+    std::vector<double> m_lsca2, m_rem, m_fu;
+    std::vector<unsigned char> m_active;
+    std::vector<double> m_ledger;  // [n_models][LG_N][nl] of the last phase of the last call
+    Exps eU{}, eJ{}, eL{};
+    double *d_partial = nullptr, *h_partial = nullptr;  // deterministic sums
 };
 
 namespace {
@@ -150,7 +178,10 @@ void free_all(dartray_grid *g) {
     void *ptrs[] = {g->d_ztab, g->d_node_child, g->d_rope, g->d_node_box, g->d_leaf_box, g->d_dirtab, g->d_kr,
                     g->d_emis, g->d_pxyz, g->d_plum, g->d_U, g->d_ULL, g->d_pend[0], g->d_pend[1], g->d_jtot,
                     g->d_flags, g->d_blocksum, g->d_total, g->d_src_idx, g->d_src_leaf, g->d_src_hint,
-                    g->d_src_pos, g->d_src_S, g->d_st, g->d_sum, g->d_stage};
+                    g->d_src_pos, g->d_src_S, g->d_st, g->d_sum, g->d_stage, g->d_Ufix, g->d_pfix,
+                    g->d_partial, g->d_mirror, g->d_mirror_pix, g->d_oct_u, g->d_oct_p, g->d_thr,
+                    g->d_fu_model, g->d_models, g->d_leaf_model, g->d_point_model, g->d_model_active,
+                    g->d_mcount, g->d_mled, g->d_mled_fix, g->d_seg_beg, g->d_seg_len, g->d_seg_out};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kPipes; ++i) {
@@ -165,6 +196,7 @@ void free_all(dartray_grid *g) {
         if (P.ev) cudaEventDestroy(P.ev);
         if (P.stream) cudaStreamDestroy(P.stream);
     }
+    if (g->h_partial) cudaFreeHost(g->h_partial);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     if (g->mev0) cudaEventDestroy(g->mev0);
@@ -192,18 +224,24 @@ int fetch_host(std::vector<T> &dst, const T *src, size_t count, bool on_device) 
     return DARTRAY_OK;
 }
 
-int occupancy_blocks(const void *kernel, int num_sms, int block = kBlock) {
+int occupancy_blocks(const void *kernel, int num_sms, int block = kBlock, int smem = 0) {
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
     return std::max(1, per_sm) * num_sms;
+}
+
+template <int NL, bool DET>
+void launch_march_det(dartray_grid *g, cudaStream_t st, int mode, const MarchArgs &A) {
+    const int blocks = g->march_blocks, sm = g->march_smem;
+    if (mode == MODE_LL) march_kernel<NL, MODE_LL, DET><<<blocks, kMarchBlock, sm, st>>>(g->G, A);
+    else if (mode == MODE_DIRECT) march_kernel<NL, MODE_DIRECT, DET><<<blocks, kMarchBlock, sm, st>>>(g->G, A);
+    else march_kernel<NL, MODE_SCATTER, DET><<<blocks, kMarchBlock, sm, st>>>(g->G, A);
 }
 
 template <int NL>
 int launch_march_nl(dartray_grid *g, cudaStream_t st, int mode, const MarchArgs &A) {
-    const int blocks = g->march_blocks;
-    if (mode == MODE_LL) march_kernel<NL, MODE_LL><<<blocks, kMarchBlock, 0, st>>>(g->G, A);
-    else if (mode == MODE_DIRECT) march_kernel<NL, MODE_DIRECT><<<blocks, kMarchBlock, 0, st>>>(g->G, A);
-    else march_kernel<NL, MODE_SCATTER><<<blocks, kMarchBlock, 0, st>>>(g->G, A);
+    if (A.det) launch_march_det<NL, true>(g, st, mode, A);
+    else launch_march_det<NL, false>(g, st, mode, A);
     ++g->launches;
     CK(cudaGetLastError());
     return DARTRAY_OK;
@@ -213,27 +251,36 @@ int launch_march(dartray_grid *g, cudaStream_t st, int mode, const MarchArgs &A)
     switch (g->nl) {
     case 1: return launch_march_nl<1>(g, st, mode, A);
     case 2: return launch_march_nl<2>(g, st, mode, A);
-    case 4: return launch_march_nl<4>(g, st, mode, A);
-    case 8: return launch_march_nl<8>(g, st, mode, A);
-    case 16: return launch_march_nl<16>(g, st, mode, A);
-    default: return fail(DARTRAY_E_INVAL, "n_lambda must be 1, 2, 4, 8 or 16");
+    default:
+        if (!launch_march_wide(g->nl, mode, A.det != 0, g->march_blocks, kMarchBlock, g->march_smem, st, g->G, A))
+            return fail(DARTRAY_E_INVAL, "n_lambda must be 1, 2, 4, 8 or 16");
+        ++g->launches;
+        CK(cudaGetLastError());
+        return DARTRAY_OK;
     }
 }
 
-// Compacted source table of a phase; returns the count in *n_src.
-int build_sources(dartray_grid *g, int mode, const float *pend_src, int *n_src) {
+// Compacted source table of a phase; returns the number of sources traced
+// in *n_src and the number of sources of the model, N_s of Eq. 10, in *n_s
+// (they differ in the octant mode, which traces the first octant only).
+int build_sources(dartray_grid *g, int mode, const float *pend_src, int *n_src, int *n_s) {
     const int n_all = mode == MODE_SCATTER ? g->n_leaf : g->n_leaf + g->n_point;
     const int nb = (n_all + kBlock - 1) / kBlock;
-    source_flags_kernel<<<nb, kBlock, 0, g->stream>>>(g->G, mode, pend_src, g->P.src_stride, g->P.src_offset,
-                                                      g->d_flags);
-    scan_blocks_kernel<<<nb, kBlock, 0, g->stream>>>(nullptr, g->d_flags, n_all, g->d_blocksum);
-    scan_offsets_kernel<<<1, 1, 0, g->stream>>>(nullptr, g->d_blocksum, nb, g->d_total);
-    scatter_compact_kernel<<<nb, kBlock, 0, g->stream>>>(g->d_flags, n_all, g->d_blocksum, g->d_src_idx);
-    g->launches += 4;
-    CK(cudaGetLastError());
     int total = 0;
-    CK(cudaMemcpyAsync(&total, g->d_total, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
-    CK(cudaStreamSynchronize(g->stream));
+    for (int pass = g->G.octant ? 0 : 1; pass < 2; ++pass) {
+        // pass 0 (octant mode): every source, for N_s; pass 1: those traced
+        source_flags_kernel<<<nb, kBlock, 0, g->stream>>>(
+            g->G, mode, pend_src, g->P.src_stride, g->P.src_offset, pass == 1 ? g->G.octant : 0,
+            mode == MODE_SCATTER && g->n_models > 1 ? g->d_model_active : nullptr, g->d_flags);
+        scan_blocks_kernel<<<nb, kBlock, 0, g->stream>>>(nullptr, g->d_flags, n_all, g->d_blocksum);
+        scan_offsets_kernel<<<1, 1, 0, g->stream>>>(nullptr, g->d_blocksum, nb, g->d_total);
+        scatter_compact_kernel<<<nb, kBlock, 0, g->stream>>>(g->d_flags, n_all, g->d_blocksum, g->d_src_idx);
+        g->launches += 4;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&total, g->d_total, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        if (pass == 0 || !g->G.octant) *n_s = total;
+    }
     if (total > 0) {
         source_table_kernel<<<(total + kBlock - 1) / kBlock, kBlock, 0, g->stream>>>(
             g->G, mode, g->d_src_idx, total, g->d_src_leaf, g->d_src_hint, g->d_src_pos, g->d_src_S);
@@ -259,12 +306,29 @@ int enqueue_flush_kernels(dartray_grid *g, Pipe &P, float *pend_dst, int force) 
     scan_apply_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, P.d_cnt, g->n_leaf, P.d_blocksum, P.d_off, P.d_cur);
     rec_scatter_kernel<<<gb, kBlock, 0, s>>>(P.d_pd, P.d_rec_n, P.d_rec_cell, P.d_rec_dir, P.d_rec_coef, g->rec_cap,
                                              g->nl, P.d_cur, P.d_srt_dir, P.d_srt_coef);
-    const int packed = g->nl == 1;
+    FlushArgs F{};
+    F.pd = P.d_pd;
+    F.n_sorted = P.d_total;
+    F.off = P.d_off;
+    F.n_leaf = g->n_leaf;
+    F.sdir = P.d_srt_dir;
+    F.scoef = P.d_srt_coef;
+    F.cap = g->rec_cap;
+    F.packed = g->nl == 1;
+    F.pend = pend_dst;
+    F.det = g->P.deterministic;
+    F.pend_fix = g->d_pfix;
+    for (int l = 0; l < kMaxLambda; ++l) F.eJ[l] = g->eJ.e[l];
+    const bool det = g->P.deterministic != 0;
     for (int l = 0; l < g->nl; ++l) {
-#define ACC(PPL) \
-    cell_accumulate_kernel<PPL><<<g->acc_blocks[PPL == 1 ? 0 : (PPL == 2 ? 1 : (PPL == 6 ? 2 : 3))], kBlock, 0, s>>>(g->G, l, P.d_pd, P.d_total, P.d_off, g->n_leaf, P.d_srt_dir, \
-                                                      P.d_srt_coef, g->rec_cap, packed, pend_dst)
-        switch (g->k_lam[l]) {
+        const int slot = g->k_lam[l] == 0 ? 0 : (g->k_lam[l] == 1 ? 1 : (g->k_lam[l] == 2 ? 2 : 3));
+        const unsigned blocks = static_cast<unsigned>(g->acc_blocks[det ? 4 + slot : slot]);
+#define ACC(PPL)                                                                              \
+    do {                                                                                      \
+        if (det) cell_accumulate_kernel<PPL, true><<<blocks, kBlock, 0, s>>>(g->G, l, F);     \
+        else cell_accumulate_kernel<PPL, false><<<blocks, kBlock, 0, s>>>(g->G, l, F);        \
+    } while (0)
+        switch (slot) {
         case 0: ACC(1); break;
         case 1: ACC(2); break;
         case 2: ACC(6); break;
@@ -272,7 +336,7 @@ int enqueue_flush_kernels(dartray_grid *g, Pipe &P, float *pend_dst, int force) 
         }
 #undef ACC
     }
-    flush_reset_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, P.d_rec_n, P.d_cnt, g->n_leaf);
+    flush_reset_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, P.d_rec_n, P.d_cnt, g->n_leaf, P.d_total, P.d_st);
     g->launches += 6 + g->nl;
     CK(cudaGetLastError());
     return DARTRAY_OK;
@@ -481,6 +545,31 @@ int status_error(const PipeDev &h, int mode) {
     return DARTRAY_OK;
 }
 
+// Deterministic sum of n floats x[0], x[stride], ... (fixed grid, partials
+// added in order on the host).
+int det_sum(dartray_grid *g, const float *x, long long n, long long stride, double *out) {
+    *out = 0.0;
+    if (n <= 0) return DARTRAY_OK;
+    det_sum_kernel<<<kSumBlocks, kBlock, 0, g->stream>>>(x, n, stride, g->d_partial);
+    ++g->launches;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(g->h_partial, g->d_partial, kSumBlocks * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    double t = 0.0;
+    for (int b = 0; b < kSumBlocks; ++b) t += g->h_partial[b];
+    *out = t;
+    return DARTRAY_OK;
+}
+
+// 60 - ceil(log2(bound)): the exponent that maps a positive bound to at most
+// 2^60 in the fixed point of the deterministic mode (0 for no bound).
+int fix_exponent(double bound) {
+    if (!(bound > 0.0) || !std::isfinite(bound)) return 0;
+    int x = 0;
+    const double f = std::frexp(bound, &x);
+    return 60 - (f == 0.5 ? x - 1 : x);
+}
+
 // One phase (mode: step 1, step 2, one scattering iteration).
 int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
     cudaStream_t s = g->stream;
@@ -488,10 +577,36 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
     if (mode == MODE_SCATTER) g->cur = 1 - g->cur;
     float *pend_src = g->d_pend[g->cur];
     float *pend_dst = g->d_pend[1 - g->cur];
-    int n_src = 0;
-    int rc = build_sources(g, mode, pend_src, &n_src);
+    int n_src = 0, n_s = 0;
+    int rc = build_sources(g, mode, pend_src, &n_src, &n_s);
     if (rc) return rc;
-    const double f_u = n_src > 0 ? 4.0 * g->P.a_rt / n_src : 0.0;  // Eq. 10
+    const double f_u = n_s > 0 ? 4.0 * g->P.a_rt / n_s : 0.0;  // Eq. 10
+    // f_U per model (batched grids: N_s counts the sources of each model)
+    if (g->n_models > 1) {
+        const int n_all = mode == MODE_SCATTER ? g->n_leaf : g->n_leaf + g->n_point;
+        std::vector<int> cnt(g->n_models, 0);
+        CK(cudaMemsetAsync(g->d_mcount, 0, g->n_models * sizeof(int), s));
+        model_count_kernel<<<(n_all + kBlock - 1) / kBlock, kBlock, 0, s>>>(g->G, g->d_flags, n_all, g->d_mcount);
+        ++g->launches;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(cnt.data(), g->d_mcount, g->n_models * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int m = 0; m < g->n_models; ++m) g->m_fu[m] = cnt[m] > 0 ? 4.0 * g->P.a_rt / cnt[m] : 0.0;
+    } else {
+        g->m_fu[0] = f_u;
+    }
+    {
+        std::vector<float> fu(g->n_models);
+        for (int m = 0; m < g->n_models; ++m) fu[m] = static_cast<float>(g->m_fu[m]);
+        CK(cudaMemcpyAsync(g->d_fu_model, fu.data(), fu.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        if (mode != MODE_LL) {
+            threshold_kernel<<<static_cast<unsigned>((nU + kBlock - 1) / kBlock), kBlock, 0, s>>>(g->G, g->d_ULL,
+                                                                                               g->d_fu_model, g->d_thr);
+            ++g->launches;
+            CK(cudaGetLastError());
+        }
+        CK(cudaStreamSynchronize(s));  // fu lives on this stack frame
+    }
     int kstart = g->P.k0;
     if (mode == MODE_SCATTER)
         for (int l = 0; l < g->nl; ++l) kstart = std::max(kstart, g->k_lam[l]);
@@ -502,10 +617,17 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
     base.src_pos = g->d_src_pos;
     base.src_S = g->d_src_S;
     base.cap = g->cap;
-    base.target = mode == MODE_LL ? g->d_ULL : g->d_U;
+    // octant mode (float sums): the traced sources deposit into scratch
+    // arrays, folded over the eight images of each cell at the end
+    const bool fold = g->G.octant && !g->P.deterministic;
+    base.target = fold ? g->d_oct_u : (mode == MODE_LL ? g->d_ULL : g->d_U);
+    float *dep_pend = fold ? g->d_oct_p : pend_dst;
     base.U_LL = g->d_ULL;
+    base.thr = g->d_thr;
+    base.mled = g->d_mled;
+    base.mled_fix = g->d_mled_fix;
     base.pend_src = pend_src;
-    base.pend_dst = pend_dst;
+    base.pend_dst = dep_pend;
     base.f_u = static_cast<float>(f_u);
     base.r_pre = static_cast<float>(g->P.r_pre);
     base.c_light = static_cast<float>(g->P.c_light);
@@ -518,6 +640,36 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
     base.max_cross = g->P.max_cross;
     base.st = g->d_st;
     base.rec_cap = g->rec_cap;
+    const bool det = g->P.deterministic != 0;
+    if (det) {
+        // Fixed-point exponents from the luminosity L_emit the phase emits
+        // per wavelength: no cell receives more RFED than
+        // 2 sqrt(3) L_emit / (L^2 c) (each ray's power crosses a cell once,
+        // over at most sqrt(3) L; a merged ray may start a little before its
+        // siblings stopped, hence the 2), and no j_sca pixel or ledger entry
+        // more than 2 L_emit; a further factor 2 of margin.
+        for (int l = 0; l < g->nl; ++l) {
+            double le = 0.0;
+            if (mode == MODE_SCATTER) {
+                const long long np = 12ll << (2 * g->k_lam[l]);
+                if ((rc = det_sum(g, pend_src + g->off_lam[l], static_cast<long long>(g->n_leaf) * np, 1, &le))) return rc;
+            } else {
+                if ((rc = det_sum(g, g->d_src_S + l, n_src, g->nl, &le))) return rc;
+                le *= 4.0 * kPi;
+            }
+            g->eU.e[l] = fix_exponent(4.0 * std::sqrt(3.0) * le / g->P.c_light);
+            g->eJ.e[l] = fix_exponent(4.0 * le);
+            g->eL.e[l] = fix_exponent(4.0 * le);
+        }
+        base.det = 1;
+        base.U_fix = g->d_Ufix;
+        base.pend_fix = g->d_pfix;
+        for (int l = 0; l < kMaxLambda; ++l) {
+            base.eU[l] = g->eU.e[l];
+            base.eJ[l] = g->eJ.e[l];
+            base.eL[l] = g->eL.e[l];
+        }
+    }
 
     // Sources are traced in batches (the phase is additive over sources and
     // U_LL is fixed during a phase, so batching does not change the result),
@@ -550,6 +702,19 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
             }
             CK(cudaMemsetAsync(pend_dst, 0, g->sca_len * sizeof(float), s));
         }
+        if (det) {
+            CK(cudaMemsetAsync(g->d_Ufix, 0, nU * sizeof(unsigned long long), s));
+            if (mode != MODE_LL) CK(cudaMemsetAsync(g->d_pfix, 0, g->sca_len * sizeof(unsigned long long), s));
+        }
+        if (g->n_models > 1) {
+            const size_t nm = static_cast<size_t>(g->n_models) * LG_N * g->nl;
+            CK(cudaMemsetAsync(g->d_mled, 0, nm * sizeof(double), s));
+            CK(cudaMemsetAsync(g->d_mled_fix, 0, nm * sizeof(unsigned long long), s));
+        }
+        if (fold) {
+            CK(cudaMemsetAsync(g->d_oct_u, 0, nU * sizeof(float), s));
+            if (mode != MODE_LL) CK(cudaMemsetAsync(g->d_oct_p, 0, g->sca_len * sizeof(float), s));
+        }
         for (int i = 0; i < kPipes; ++i) {
             Pipe &P = g->pipe[i];
             P.active = false;
@@ -561,6 +726,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
         }
         DevStats fresh = snap;
         std::memset(fresh.ledger, 0, sizeof fresh.ledger);
+        std::memset(fresh.ledger_fix, 0, sizeof fresh.ledger_fix);
         CK(cudaMemcpyAsync(g->d_st, &fresh, sizeof(DevStats), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));  // the pipelines start after the setup
         std::unique_ptr<PhaseTiming> tm;
@@ -597,7 +763,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
                 if (P.active) {
                     any = true;
                     for (int w = 0; w < kWavesAhead; ++w)
-                        if ((rc = enqueue_wave(g, P, i, mode, base, pend_dst, tm.get()))) return rc;
+                        if ((rc = enqueue_wave(g, P, i, mode, base, dep_pend, tm.get()))) return rc;
                     CK(cudaMemcpyAsync(P.h_pd, P.d_pd, sizeof(PipeDev), cudaMemcpyDeviceToHost, P.stream));
                     CK(cudaEventRecord(P.ev, P.stream));
                     inflight[i] = true;
@@ -640,7 +806,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
         if (!overflow) {
             // last records of both pipelines
             for (int i = 0; i < kPipes && mode != MODE_LL; ++i) {
-                if ((rc = enqueue_flush(g, g->pipe[i], pend_dst, 1, tm.get(), i))) return rc;
+                if ((rc = enqueue_flush(g, g->pipe[i], dep_pend, 1, tm.get(), i))) return rc;
                 CK(cudaStreamSynchronize(g->pipe[i].stream));
                 if (tm) tm->collect(i);
             }
@@ -662,9 +828,37 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
                 CK(cudaMemcpyAsync(&ps, g->pipe[i].d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
                 out.cnt[CT_FLUSH] += ps.cnt[CT_FLUSH];
+                out.cnt[CT_REC] += ps.cnt[CT_REC];
             }
             CK(cudaMemcpyAsync(g->d_st, &out, sizeof(DevStats), cudaMemcpyHostToDevice, s));
             std::memcpy(res->ledger, out.ledger, sizeof res->ledger);
+            if (det)
+                for (int sl = 0; sl < LG_N; ++sl)
+                    for (int l = 0; l < g->nl; ++l)
+                        res->ledger[sl][l] = std::ldexp(static_cast<double>(out.ledger_fix[sl][l]), -g->eL.e[l]);
+            if (g->G.octant)  // the traced sources stand for their images in all eight octants
+                for (int sl = 0; sl < LG_N; ++sl)
+                    for (int l = 0; l < g->nl; ++l) res->ledger[sl][l] *= 8.0;
+            if (g->n_models > 1) {
+                // per-model ledgers; the grid's ledger is their sum
+                const size_t nm = static_cast<size_t>(g->n_models) * LG_N * g->nl;
+                std::vector<unsigned long long> raw(nm);
+                if (det) CK(cudaMemcpyAsync(raw.data(), g->d_mled_fix, nm * 8, cudaMemcpyDeviceToHost, s));
+                else CK(cudaMemcpyAsync(raw.data(), g->d_mled, nm * 8, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                std::memset(res->ledger, 0, sizeof res->ledger);
+                for (size_t i = 0; i < nm; ++i) {
+                    const int l = static_cast<int>(i % g->nl), sl = static_cast<int>((i / g->nl) % LG_N);
+                    double v;
+                    if (det) v = std::ldexp(static_cast<double>(raw[i]), -g->eL.e[l]);
+                    else std::memcpy(&v, &raw[i], sizeof v);
+                    g->m_ledger[i] = v;
+                    res->ledger[sl][l] += v;
+                }
+            } else {
+                for (int sl = 0; sl < LG_N; ++sl)
+                    for (int l = 0; l < g->nl; ++l) g->m_ledger[static_cast<size_t>(sl) * g->nl + l] = res->ledger[sl][l];
+            }
             std::memcpy(res->cnt, out.cnt, sizeof res->cnt);
             g->rays_per_src[mode] = std::max(rps_floor, max_rps);
             g->batches += batches;
@@ -677,14 +871,55 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
     }
     res->f_u = f_u;
     res->pend_sum = 0.0;
+    if (det) {
+        // fixed point -> float: U (step 2 from zero, an iteration on top of
+        // U_LL), U_LL in step 1, the pending j_sca rows
+        const unsigned ub = static_cast<unsigned>((nU + kBlock - 1) / kBlock);
+        fix_to_u_kernel<<<ub, kBlock, 0, s>>>(g->G, g->d_Ufix, mode == MODE_SCATTER ? g->d_ULL : nullptr, g->eU,
+                                              mode == MODE_LL ? g->d_ULL : g->d_U);
+        ++g->launches;
+        if (mode != MODE_LL) {
+            for (int l = 0; l < g->nl; ++l) {
+                fix_to_jsca_kernel<<<8 * g->num_sms, kBlock, 0, s>>>(g->G, l, g->d_pfix, g->eJ, pend_dst);
+                ++g->launches;
+            }
+        }
+        CK(cudaGetLastError());
+    }
+    if (fold) {
+        const unsigned ub = static_cast<unsigned>((nU + kBlock - 1) / kBlock);
+        octant_fold_u_kernel<<<ub, kBlock, 0, s>>>(g->G, g->d_oct_u, mode == MODE_SCATTER ? g->d_ULL : nullptr,
+                                                   mode == MODE_LL ? g->d_ULL : g->d_U);
+        ++g->launches;
+        if (mode != MODE_LL) {
+            for (int l = 0; l < g->nl; ++l) {
+                octant_fold_jsca_kernel<<<8 * g->num_sms, kBlock, 0, s>>>(g->G, l, g->d_oct_p, pend_dst);
+                ++g->launches;
+            }
+        }
+        CK(cudaGetLastError());
+    }
     if (mode != MODE_LL) {
-        CK(cudaMemsetAsync(g->d_sum, 0, sizeof(double), s));
-        accumulate_pending_kernel<<<4 * g->num_sms, kBlock, 0, s>>>(pend_dst, g->d_jtot, g->sca_len, g->d_sum);
+        add_pending_kernel<<<8 * g->num_sms, kBlock, 0, s>>>(pend_dst, g->d_jtot, g->sca_len);
         ++g->launches;
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(g->d_ULL, g->d_U, nU * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(&res->pend_sum, g->d_sum, sizeof(double), cudaMemcpyDeviceToHost, s));
+        // remaining scattered luminosity per model (sum over its wavelength
+        // blocks), in a fixed order
+        const int nseg = g->n_models * g->nl;
+        std::vector<double> seg(nseg);
+        segment_sum_kernel<<<nseg, kBlock, 0, s>>>(pend_dst, g->d_seg_beg, g->d_seg_len, g->d_seg_out);
+        ++g->launches;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(seg.data(), g->d_seg_out, nseg * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        for (int m = 0; m < g->n_models; ++m) {
+            double t = 0.0;
+            for (int l = 0; l < g->nl; ++l) t += seg[m * g->nl + l];
+            res->pend_sum += t;
+            if (mode == MODE_DIRECT) g->m_lsca2[m] = t;
+            g->m_rem[m] = g->m_lsca2[m] > 0 ? t / g->m_lsca2[m] : 0.0;
+        }
     }
     return DARTRAY_OK;
 }
@@ -705,6 +940,7 @@ void fill_stats(const dartray_grid *g, const PhaseResult &r, dartray_stats *st) 
     st->sources = r.cnt[CT_SOURCES];
     st->jsca_pixels = r.cnt[CT_JPIX];
     st->flushes = r.cnt[CT_FLUSH];
+    st->records = r.cnt[CT_REC];
     for (int l = 0; l < g->nl; ++l) {
         const double w = g->G.albedo[l];
         st->emitted[l] = r.ledger[LG_EMITTED][l];
@@ -768,85 +1004,186 @@ int dartray_params_default(dartray_params *p) {
     p->profile = 0;
     p->deposit_direct = 0;
     p->deposit_records = 0;
+    p->deterministic = 0;
+    p->octant = 0;
     return DARTRAY_OK;
 }
 
-int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *params, void *cuda_stream,
-                        dartray_grid **out) {
+}  // extern "C"
+
+namespace {
+
+// Append the topology of one model to the forest of a grid: node, leaf and
+// face-link indices shift by the nodes and leaves already there.
+void append_topology(HostTopo *all, const HostTopo &t, int node_off, int leaf_off) {
+    for (const int32_t c : t.node_child) all->node_child.push_back(c >= 0 ? c + node_off : c - leaf_off);
+    all->node_box.insert(all->node_box.end(), t.node_box.begin(), t.node_box.end());
+    all->leaf_box.insert(all->leaf_box.end(), t.leaf_box.begin(), t.leaf_box.end());
+    for (const int32_t n : t.leaf_node) all->leaf_node.push_back(n + node_off);
+    for (const int32_t code : t.leaf_rope) {
+        // >= 0 a node; -1 the boundary; -(leaf + 2) a larger leaf;
+        // kRopeSameSize - leaf a leaf of the same size
+        all->leaf_rope.push_back(code >= 0 ? code + node_off : (code == kRopeBoundary ? code : code - leaf_off));
+    }
+    all->max_depth = std::max(all->max_depth, t.max_depth);
+}
+
+int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_params *params, void *cuda_stream,
+                dartray_grid **out) {
     g_last_error.clear();
-    if (!desc || !out) return fail(DARTRAY_E_INVAL, "null argument");
+    if (!descs || !out) return fail(DARTRAY_E_INVAL, "null argument");
     *out = nullptr;
+    if (n_models < 1 || n_models > kMaxModels) return fail(DARTRAY_E_INVAL, "n_models must be in [1, 4096]");
+    const dartray_grid_desc *desc = &descs[0];
     dartray_params P;
     if (params) P = *params;
     else dartray_params_default(&P);
     const int nl = desc->n_lambda;
     if (nl != 1 && nl != 2 && nl != 4 && nl != 8 && nl != 16)
         return fail(DARTRAY_E_INVAL, "n_lambda must be 1, 2, 4, 8 or 16");
-    if (desc->n_leaf < 1 || desc->n_nodes < 1 || desc->n_point < 0) return fail(DARTRAY_E_INVAL, "bad sizes");
+    long long tot_leaf = 0, tot_nodes = 0, tot_point = 0;
+    for (int m = 0; m < n_models; ++m) {
+        const dartray_grid_desc &d = descs[m];
+        if (d.n_leaf < 1 || d.n_nodes < 1 || d.n_point < 0) return fail(DARTRAY_E_INVAL, "bad sizes");
+        if (d.n_lambda != nl) return fail(DARTRAY_E_INVAL, "the models of a batch must share n_lambda");
+        tot_leaf += d.n_leaf;
+        tot_nodes += d.n_nodes;
+        tot_point += d.n_point;
+    }
+    if (tot_leaf >= (1ll << 29) || tot_nodes >= (1ll << 30) || tot_point >= (1ll << 30))
+        return fail(DARTRAY_E_INVAL, "too many cells or points in total");
     if (P.k0 < 0 || P.k0 > 13 || P.k_ray_max < P.k0 || P.k_ray_max > 13 || P.k_sca_cap < 0 || P.k_sca_cap > 3 ||
         P.n_fwhm < 1 || P.n_rays_min < 0 || P.n_rays_max < 0 || P.src_stride < 1 || P.src_offset < 0 ||
         P.src_offset >= P.src_stride || P.max_cross < 1 || P.max_waves < 1 ||
         (P.queue_rays != 0 && P.queue_rays < 1024) || P.deposit_records < 0 ||
-        !(P.c_light > 0) || P.a_rt < 0)
+        !(P.c_light > 0) || P.a_rt < 0 || P.deterministic < 0 || P.deterministic > 1 || P.octant < 0 ||
+        P.octant > 1 || (P.octant && P.src_stride != 1))
         return fail(DARTRAY_E_INVAL, "invalid parameters");
+    if (P.octant && n_models > 1) return fail(DARTRAY_E_INVAL, "the octant mode takes a single model");
+    if (n_models > 1 && static_cast<long long>(n_models) * LG_N * nl * 8 > 32768)
+        return fail(DARTRAY_E_INVAL, "a batch holds at most 4096 / (6 n_lambda) models");
     const bool on_dev = desc->inputs_on_device != 0;
-    // host copies of the topology for validation and face links
-    std::vector<int32_t> fc, lon;
-    int rc = fetch_host(fc, desc->first_child, desc->n_nodes, on_dev);
-    if (rc) return rc;
-    rc = fetch_host(lon, desc->leaf_of_node, desc->n_nodes, on_dev);
-    if (rc) return rc;
     std::vector<float> alb, gg;
-    rc = fetch_host(alb, desc->albedo, nl, on_dev);
+    int rc = fetch_host(alb, desc->albedo, nl, on_dev);
     if (rc) return rc;
     rc = fetch_host(gg, desc->g, nl, on_dev);
     if (rc) return rc;
     for (int l = 0; l < nl; ++l)
         if (!(alb[l] >= 0.f && alb[l] <= 1.f) || !(gg[l] > -1.f && gg[l] < 1.f))
             return fail(DARTRAY_E_INVAL, "albedo must be in [0,1] and g in (-1,1)");
+    for (int m = 1; m < n_models; ++m) {
+        std::vector<float> a2, g2;
+        if ((rc = fetch_host(a2, descs[m].albedo, nl, descs[m].inputs_on_device != 0)) ||
+            (rc = fetch_host(g2, descs[m].g, nl, descs[m].inputs_on_device != 0)))
+            return rc;
+        if (a2 != alb || g2 != gg) return fail(DARTRAY_E_INVAL, "the models of a batch must share albedo and g");
+    }
 
     dartray_grid *g = new dartray_grid();
     g->P = P;
     g->stream = static_cast<cudaStream_t>(cuda_stream);
     g->nl = nl;
-    g->n_leaf = desc->n_leaf;
-    g->n_nodes = desc->n_nodes;
-    g->n_point = desc->n_point;
+    g->n_leaf = static_cast<int>(tot_leaf);
+    g->n_nodes = static_cast<int>(tot_nodes);
+    g->n_point = static_cast<int>(tot_point);
+    g->n_models = n_models;
     auto bail = [&](int code) {
         free_all(g);
         delete g;
         return code;
     };
-    std::string err = build_topology(desc->nroot, desc->root_lo, desc->root_size, desc->n_nodes, desc->n_leaf,
-                                     fc.data(), lon.data(), &g->topo);
-    if (!err.empty()) return bail(fail(DARTRAY_E_INVAL, err));
+    // topology of every model, validated and appended to one forest (node,
+    // leaf and face-link indices shifted by the models before it)
+    std::vector<int32_t> fc, lon;  // of the model built last (the only one in the octant mode)
+    std::vector<ModelDev> models(n_models);
+    std::string err;
+    long long node_off = 0, leaf_off = 0, point_off = 0;
+    for (int m = 0; m < n_models; ++m) {
+        const dartray_grid_desc &d = descs[m];
+        const bool dev_m = d.inputs_on_device != 0;
+        if ((rc = fetch_host(fc, d.first_child, d.n_nodes, dev_m)) || (rc = fetch_host(lon, d.leaf_of_node, d.n_nodes, dev_m)))
+            return bail(rc);
+        HostTopo t;
+        err = build_topology(d.nroot, d.root_lo, d.root_size, d.n_nodes, d.n_leaf, fc.data(), lon.data(), &t);
+        if (!err.empty()) return bail(fail(DARTRAY_E_INVAL, n_models > 1 ? "model " + std::to_string(m) + ": " + err : err));
+        append_topology(&g->topo, t, static_cast<int>(node_off), static_cast<int>(leaf_off));
+        ModelDev &M = models[m];
+        for (int a = 0; a < 3; ++a) {
+            M.nroot[a] = d.nroot[a];
+            M.root_lo[a] = static_cast<float>(d.root_lo[a]);
+        }
+        M.root_size = static_cast<float>(d.root_size);
+        M.node0 = static_cast<int>(node_off);
+        M.r_pre = static_cast<float>(P.r_pre >= 0 ? P.r_pre
+                                                  : 0.15 * d.root_size * std::max({d.nroot[0], d.nroot[1], d.nroot[2]}));
+        g->m_leaf0.push_back(leaf_off);
+        g->m_nleaf.push_back(d.n_leaf);
+        g->m_point0.push_back(point_off);
+        node_off += d.n_nodes;
+        leaf_off += d.n_leaf;
+        point_off += d.n_point;
+    }
+    std::vector<int32_t> mirror;
+    if (P.octant) {
+        // the octant mode needs a model symmetric under the reflections about
+        // the planes through its centre: topology, dust and emission alike
+        err = build_mirrors(desc->nroot, desc->root_lo, desc->root_size, fc.data(), lon.data(), g->topo, &mirror);
+        if (!err.empty()) return bail(fail(DARTRAY_E_INVAL, "octant mode: " + err));
+        std::vector<float> kr, em, pxyz, plum;
+        const size_t nU0 = static_cast<size_t>(desc->n_leaf) * nl;
+        if ((rc = fetch_host(kr, desc->kappa_rho, nU0, on_dev)) || (rc = fetch_host(em, desc->emissivity, nU0, on_dev)) ||
+            (rc = fetch_host(pxyz, desc->point_xyz, 3ull * desc->n_point, on_dev)) ||
+            (rc = fetch_host(plum, desc->point_lum, static_cast<size_t>(desc->n_point) * nl, on_dev)))
+            return bail(rc);
+        for (int m = 1; m < 8; ++m)
+            for (int64_t c = 0; c < desc->n_leaf; ++c) {
+                const int64_t cm = mirror[static_cast<size_t>(m - 1) * desc->n_leaf + c];
+                for (int l = 0; l < nl; ++l)
+                    if (kr[c * nl + l] != kr[cm * nl + l] || em[c * nl + l] != em[cm * nl + l])
+                        return bail(fail(DARTRAY_E_INVAL, "octant mode: kappa_rho or emissivity not mirror-symmetric"));
+            }
+        for (int m = 1; m < 8; ++m)
+            for (int i = 0; i < desc->n_point; ++i) {
+                float q[3];
+                for (int a = 0; a < 3; ++a) {
+                    const double c = desc->root_lo[a] + 0.5 * desc->nroot[a] * desc->root_size;
+                    q[a] = ((m >> a) & 1) ? static_cast<float>(2.0 * c - pxyz[3 * i + a]) : pxyz[3 * i + a];
+                }
+                bool found = false;
+                for (int j = 0; j < desc->n_point && !found; ++j)
+                    found = pxyz[3 * j] == q[0] && pxyz[3 * j + 1] == q[1] && pxyz[3 * j + 2] == q[2] &&
+                            std::equal(plum.begin() + static_cast<long>(i) * nl, plum.begin() + static_cast<long>(i + 1) * nl,
+                                       plum.begin() + static_cast<long>(j) * nl);
+                if (!found) return bail(fail(DARTRAY_E_INVAL, "octant mode: point sources not mirror-symmetric"));
+            }
+    }
     if (cudaGetDevice(&g->device) != cudaSuccess) return bail(fail(DARTRAY_E_CUDA, "no CUDA device"));
     cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
-    if (g->P.r_pre < 0) g->P.r_pre = 0.15 * desc->root_size * std::max({desc->nroot[0], desc->nroot[1], desc->nroot[2]});
+    g->P.r_pre = models[0].r_pre;
 
     // j_sca layout (Eq. 5)
     long long off = 0;
     for (int l = 0; l < nl; ++l) {
         g->k_lam[l] = k_hp_host(gg[l], P.n_fwhm, P.k_sca_cap);
         g->off_lam[l] = off;
-        off += static_cast<long long>(desc->n_leaf) * (12ll << (2 * g->k_lam[l]));
+        off += tot_leaf * (12ll << (2 * g->k_lam[l]));
     }
     g->sca_len = off;
 
-    const size_t nU = static_cast<size_t>(desc->n_leaf) * nl;
+    const size_t nU = static_cast<size_t>(tot_leaf) * nl;
     const long long ndir = dir_tab_offset(kDirTabLevels + 1);
     // automatic sizes: large enough for the biggest waves of galaxy-sized
     // grids, small for small grids
     g->cap = P.queue_rays > 0 ? P.queue_rays
-                              : std::min<long long>(1ll << 27, std::max<long long>(1ll << 20, 512ll * desc->n_leaf));
+                              : std::min<long long>(1ll << 27, std::max<long long>(1ll << 20, 512ll * tot_leaf));
     g->rec_cap = P.deposit_direct ? 0
                  : (P.deposit_records > 0 ? P.deposit_records
-                                          : std::min<long long>(1ll << 28, std::max<long long>(1ll << 20, 1024ll * desc->n_leaf)));
+                                          : std::min<long long>(1ll << 28, std::max<long long>(1ll << 20, 1024ll * tot_leaf)));
     // merge table: low lists are far smaller than waves; a wave whose low list
     // does not fit is retried with a smaller source batch
     g->hcap = 1;
     while (g->hcap < std::min<long long>(2 * g->cap, 1ll << 27)) g->hcap <<= 1;
-    const int n_all = desc->n_leaf + desc->n_point;
+    const int n_all = static_cast<int>(tot_leaf + tot_point);
     const int nblk = (n_all + kBlock - 1) / kBlock;
 #define AL(ptr, cnt)                                                                              \
     do {                                                                                          \
@@ -854,16 +1191,30 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
         if (e_ != cudaSuccess)                                                                    \
             return bail(fail(DARTRAY_E_NOMEM, std::string("cudaMalloc ") + #ptr + ": " + cudaGetErrorString(e_))); \
     } while (0)
-    AL(g->d_node_child, desc->n_nodes);
-    AL(g->d_node_box, desc->n_nodes);
-    AL(g->d_leaf_box, desc->n_leaf);
-    AL(g->d_rope, static_cast<size_t>(desc->n_leaf) * 6);
+    AL(g->d_node_child, tot_nodes);
+    AL(g->d_node_box, tot_nodes);
+    AL(g->d_leaf_box, tot_leaf);
+    AL(g->d_rope, static_cast<size_t>(tot_leaf) * 6);
     AL(g->d_dirtab, ndir);
     AL(g->d_ztab, static_cast<size_t>(ndir) * nl);
     AL(g->d_kr, nU);
     AL(g->d_emis, nU);
-    AL(g->d_pxyz, static_cast<size_t>(desc->n_point) * 3);
-    AL(g->d_plum, static_cast<size_t>(desc->n_point) * nl);
+    AL(g->d_pxyz, static_cast<size_t>(tot_point) * 3);
+    AL(g->d_plum, static_cast<size_t>(tot_point) * nl);
+    AL(g->d_thr, nU);
+    AL(g->d_fu_model, n_models);
+    AL(g->d_mcount, n_models);
+    AL(g->d_model_active, n_models);
+    AL(g->d_mled, static_cast<size_t>(n_models) * LG_N * nl);
+    AL(g->d_mled_fix, static_cast<size_t>(n_models) * LG_N * nl);
+    AL(g->d_seg_beg, static_cast<size_t>(n_models) * nl);
+    AL(g->d_seg_len, static_cast<size_t>(n_models) * nl);
+    AL(g->d_seg_out, static_cast<size_t>(n_models) * nl);
+    if (n_models > 1) {
+        AL(g->d_models, n_models);
+        AL(g->d_leaf_model, tot_leaf);
+        AL(g->d_point_model, tot_point);
+    }
     AL(g->d_U, nU);
     AL(g->d_ULL, nU);
     AL(g->d_pend[0], g->sca_len);
@@ -879,7 +1230,12 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
     AL(g->d_src_S, static_cast<size_t>(n_all) * nl);
     AL(g->d_st, 1);
     AL(g->d_sum, 1);
-    const int nblk_leaf = (desc->n_leaf + kBlock - 1) / kBlock;
+    AL(g->d_partial, kSumBlocks);
+    if (P.deterministic) {
+        AL(g->d_Ufix, nU);
+        AL(g->d_pfix, g->sca_len);
+    }
+    const int nblk_leaf = static_cast<int>((tot_leaf + kBlock - 1) / kBlock);
     for (int p = 0; p < kPipes; ++p) {
         Pipe &P = g->pipe[p];
         for (int i = 0; i < 2; ++i) {
@@ -903,9 +1259,9 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
                 AL(P.d_rec_coef, static_cast<size_t>(g->rec_cap) * nl);
                 AL(P.d_srt_coef, static_cast<size_t>(g->rec_cap) * nl);
             }
-            AL(P.d_cnt, desc->n_leaf);
-            AL(P.d_off, desc->n_leaf);
-            AL(P.d_cur, desc->n_leaf);
+            AL(P.d_cnt, tot_leaf);
+            AL(P.d_off, tot_leaf);
+            AL(P.d_cur, tot_leaf);
             AL(P.d_rec_n, 1);
             AL(P.d_blocksum, nblk_leaf + 1);
             AL(P.d_total, 1);
@@ -918,17 +1274,46 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
             cudaMemsetAsync(P.d_st, 0, sizeof(DevStats), g->stream) != cudaSuccess)
             return bail(fail(DARTRAY_E_CUDA, "memset failed"));
     }
-#undef AL
     cudaStream_t s = g->stream;
     auto up = [&](auto *dst, const auto *src, size_t cnt) { return copy_in(dst, src, cnt, false, s); };
-    if ((rc = up(g->d_node_child, g->topo.node_child.data(), desc->n_nodes))) return bail(rc);
-    if ((rc = up(reinterpret_cast<float *>(g->d_node_box), g->topo.node_box.data(), 4ull * desc->n_nodes))) return bail(rc);
-    if ((rc = up(reinterpret_cast<float *>(g->d_leaf_box), g->topo.leaf_box.data(), 4ull * desc->n_leaf))) return bail(rc);
-    if ((rc = up(g->d_rope, g->topo.leaf_rope.data(), 6ull * desc->n_leaf))) return bail(rc);
-    if ((rc = copy_in(g->d_kr, desc->kappa_rho, nU, on_dev, s))) return bail(rc);
-    if ((rc = copy_in(g->d_emis, desc->emissivity, nU, on_dev, s))) return bail(rc);
-    if ((rc = copy_in(g->d_pxyz, desc->point_xyz, 3ull * desc->n_point, on_dev, s))) return bail(rc);
-    if ((rc = copy_in(g->d_plum, desc->point_lum, static_cast<size_t>(desc->n_point) * nl, on_dev, s))) return bail(rc);
+    if ((rc = up(g->d_node_child, g->topo.node_child.data(), tot_nodes))) return bail(rc);
+    if ((rc = up(reinterpret_cast<float *>(g->d_node_box), g->topo.node_box.data(), 4ull * tot_nodes))) return bail(rc);
+    if ((rc = up(reinterpret_cast<float *>(g->d_leaf_box), g->topo.leaf_box.data(), 4ull * tot_leaf))) return bail(rc);
+    if ((rc = up(g->d_rope, g->topo.leaf_rope.data(), 6ull * tot_leaf))) return bail(rc);
+    std::vector<uint16_t> leaf_model, point_model;
+    for (int m = 0; m < n_models; ++m) {
+        const dartray_grid_desc &d = descs[m];
+        const bool dev_m = d.inputs_on_device != 0;
+        const size_t l0 = static_cast<size_t>(g->m_leaf0[m]) * nl, p0 = static_cast<size_t>(g->m_point0[m]);
+        const size_t nUm = static_cast<size_t>(d.n_leaf) * nl;
+        if ((rc = copy_in(g->d_kr + l0, d.kappa_rho, nUm, dev_m, s)) || (rc = copy_in(g->d_emis + l0, d.emissivity, nUm, dev_m, s)) ||
+            (rc = copy_in(g->d_pxyz + 3 * p0, d.point_xyz, 3ull * d.n_point, dev_m, s)) ||
+            (rc = copy_in(g->d_plum + p0 * nl, d.point_lum, static_cast<size_t>(d.n_point) * nl, dev_m, s)))
+            return bail(rc);
+        leaf_model.insert(leaf_model.end(), d.n_leaf, static_cast<uint16_t>(m));
+        point_model.insert(point_model.end(), d.n_point, static_cast<uint16_t>(m));
+    }
+    if (n_models > 1) {
+        if ((rc = up(g->d_models, models.data(), n_models)) || (rc = up(g->d_leaf_model, leaf_model.data(), leaf_model.size())) ||
+            (rc = up(g->d_point_model, point_model.data(), point_model.size())))
+            return bail(rc);
+    }
+    // per-model host state and segments of the j_sca array (model, wavelength)
+    g->m_lsca2.assign(n_models, 0.0);
+    g->m_rem.assign(n_models, 0.0);
+    g->m_active.assign(n_models, 1);
+    g->m_ledger.assign(static_cast<size_t>(n_models) * LG_N * nl, 0.0);
+    g->m_fu.assign(n_models, 0.0);
+    {
+        std::vector<long long> beg, len;
+        for (int m = 0; m < n_models; ++m)
+            for (int l = 0; l < nl; ++l) {
+                const long long np = 12ll << (2 * g->k_lam[l]);
+                beg.push_back(g->off_lam[l] + g->m_leaf0[m] * np);
+                len.push_back(static_cast<long long>(g->m_nleaf[m]) * np);
+            }
+        if ((rc = up(g->d_seg_beg, beg.data(), beg.size())) || (rc = up(g->d_seg_len, len.data(), len.size()))) return bail(rc);
+    }
     if (cudaMemsetAsync(g->d_U, 0, nU * sizeof(float), s) != cudaSuccess ||
         cudaMemsetAsync(g->d_ULL, 0, nU * sizeof(float), s) != cudaSuccess ||
         cudaMemsetAsync(g->d_pend[0], 0, g->sca_len * sizeof(float), s) != cudaSuccess ||
@@ -945,10 +1330,14 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
         G.root_lo[a] = static_cast<float>(desc->root_lo[a]);
     }
     G.root_size = static_cast<float>(desc->root_size);
-    G.n_nodes = desc->n_nodes;
-    G.n_leaf = desc->n_leaf;
+    G.n_nodes = static_cast<int>(tot_nodes);
+    G.n_leaf = static_cast<int>(tot_leaf);
     G.nl = nl;
-    G.n_point = desc->n_point;
+    G.n_point = static_cast<int>(tot_point);
+    G.n_models = n_models;
+    G.models = g->d_models;
+    G.leaf_model = g->d_leaf_model;
+    G.point_model = g->d_point_model;
     G.node_child = g->d_node_child;
     G.node_box = g->d_node_box;
     G.leaf_box = g->d_leaf_box;
@@ -966,30 +1355,67 @@ int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *par
         G.k_lam[l] = g->k_lam[l];
         G.off_lam[l] = g->off_lam[l];
     }
+    G.octant = P.octant;
+    for (int a = 0; a < 3; ++a)
+        G.centre[a] = static_cast<float>(desc->root_lo[a] + 0.5 * desc->nroot[a] * desc->root_size);
+    if (P.octant) {
+        AL(g->d_mirror, mirror.size());
+        AL(g->d_mirror_pix, 7 * kMirrorPix);
+        if (!P.deterministic) {
+            AL(g->d_oct_u, nU);
+            AL(g->d_oct_p, g->sca_len);
+        }
+        if ((rc = up(g->d_mirror, mirror.data(), mirror.size()))) return bail(rc);
+        mirror_pix_kernel<<<(7 * kMirrorPix + kBlock - 1) / kBlock, kBlock, 0, s>>>(g->d_mirror_pix);
+        ++g->launches;
+        G.mirror = g->d_mirror;
+        G.mirror_pix = g->d_mirror_pix;
+    }
     ztab_kernel<<<static_cast<unsigned>((ndir + kBlock - 1) / kBlock), kBlock, 0, s>>>(G, g->d_ztab, ndir);
     ++g->launches;
     // the expansion kernel runs one block per resident slot (its ranges are
     // spread over the warps it has)
-    g->acc_blocks[0] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<1>), g->num_sms);
-    g->acc_blocks[1] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<2>), g->num_sms);
-    g->acc_blocks[2] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<6>), g->num_sms);
-    g->acc_blocks[3] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<24>), g->num_sms);
+    g->acc_blocks[0] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<1, false>), g->num_sms);
+    g->acc_blocks[1] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<2, false>), g->num_sms);
+    g->acc_blocks[2] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<6, false>), g->num_sms);
+    g->acc_blocks[3] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<24, false>), g->num_sms);
+    g->acc_blocks[4] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<1, true>), g->num_sms);
+    g->acc_blocks[5] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<2, true>), g->num_sms);
+    g->acc_blocks[6] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<6, true>), g->num_sms);
+    g->acc_blocks[7] = occupancy_blocks(reinterpret_cast<const void *>(cell_accumulate_kernel<24, true>), g->num_sms);
+    // batched grids: the per-model ledgers live in dynamic shared memory
+    g->march_smem = n_models > 1 ? n_models * LG_N * nl * static_cast<int>(sizeof(unsigned long long)) : 0;
     switch (nl) {
-    case 1: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<1, MODE_SCATTER>), g->num_sms, kMarchBlock); break;
-    case 2: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<2, MODE_SCATTER>), g->num_sms, kMarchBlock); break;
-    case 4: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<4, MODE_SCATTER>), g->num_sms, kMarchBlock); break;
-    case 8: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<8, MODE_SCATTER>), g->num_sms, kMarchBlock); break;
-    default: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<16, MODE_SCATTER>), g->num_sms, kMarchBlock); break;
+    case 1: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<1, MODE_SCATTER, false>), g->num_sms, kMarchBlock, g->march_smem); break;
+    case 2: g->march_blocks = occupancy_blocks(reinterpret_cast<const void *>(march_kernel<2, MODE_SCATTER, false>), g->num_sms, kMarchBlock, g->march_smem); break;
+    default: g->march_blocks = std::max(1, march_wide_blocks_per_sm(nl, kMarchBlock, g->march_smem)) * g->num_sms; break;
     }
+    if (cudaMallocHost(reinterpret_cast<void **>(&g->h_partial), kSumBlocks * sizeof(double)) != cudaSuccess)
+        return bail(fail(DARTRAY_E_NOMEM, "pinned host buffer"));
     if (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess ||
         cudaEventCreate(&g->mev0) != cudaSuccess || cudaEventCreate(&g->mev1) != cudaSuccess)
         return bail(fail(DARTRAY_E_CUDA, "event create failed"));
+#undef AL
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return bail(fail(DARTRAY_E_CUDA, cudaGetErrorString(e)));
     const cudaError_t e2 = cudaGetLastError();
     if (e2 != cudaSuccess) return bail(fail(DARTRAY_E_CUDA, cudaGetErrorString(e2)));
     *out = g;
     return DARTRAY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *params, void *cuda_stream,
+                        dartray_grid **out) {
+    return create_grid(desc, 1, params, cuda_stream, out);
+}
+
+int dartray_grid_create_batch(const dartray_grid_desc *descs, int32_t n_models, const dartray_params *params,
+                              void *cuda_stream, dartray_grid **out) {
+    return create_grid(descs, n_models, params, cuda_stream, out);
 }
 
 int dartray_direct(dartray_grid *g, dartray_stats *stats) {
@@ -1003,6 +1429,9 @@ int dartray_direct(dartray_grid *g, dartray_stats *stats) {
     const long long l0 = g->launches;
     g->march_ms = g->flush_ms = g->busy_ms = g->march_sum_ms = 0.0;
     g->march_launches = g->restarts = g->batches = 0;
+    // every model of a batch takes part in the scattering iterations again
+    std::fill(g->m_active.begin(), g->m_active.end(), 1);
+    CK(cudaMemcpyAsync(g->d_model_active, g->m_active.data(), g->n_models, cudaMemcpyHostToDevice, g->stream));
     CK(cudaEventRecord(g->ev0, g->stream));
     PhaseResult r1{}, r2{};
     if ((rc = run_phase(g, MODE_LL, &r1))) return rc;
@@ -1043,7 +1472,20 @@ int dartray_scatter_iter(dartray_grid *g, double *remaining_frac, dartray_stats 
     if ((rc = run_phase(g, MODE_SCATTER, &r))) return rc;
     CK(cudaEventRecord(g->ev1, g->stream));
     CK(cudaEventSynchronize(g->ev1));
-    if (remaining_frac) *remaining_frac = g->l_sca2 > 0 ? r.pend_sum / g->l_sca2 : 0.0;
+    double rem = g->l_sca2 > 0 ? r.pend_sum / g->l_sca2 : 0.0;
+    if (g->n_models > 1) {
+        // batched grids: a model whose remaining fraction fell below f_L stops
+        // emitting (as a loop over single models would stop it); the call
+        // returns the largest remaining fraction
+        rem = 0.0;
+        for (int m = 0; m < g->n_models; ++m) {
+            rem = std::max(rem, g->m_rem[m]);
+            if (g->m_rem[m] < g->P.f_l) g->m_active[m] = 0;
+        }
+        CK(cudaMemcpyAsync(g->d_model_active, g->m_active.data(), g->n_models, cudaMemcpyHostToDevice, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+    }
+    if (remaining_frac) *remaining_frac = rem;
     if (stats) {
         fill_stats(g, r, stats);
         float ms = 0.f;
@@ -1109,6 +1551,7 @@ int dartray_map(dartray_grid *g, const double observer[3], int32_t nside_k, int3
     g_last_error.clear();
     if (!g || !observer || !map) return fail(DARTRAY_E_INVAL, "null argument");
     if (nside_k < 0 || nside_k > 10 || max_sub < 0 || max_sub > 6) return fail(DARTRAY_E_INVAL, "bad map size");
+    if (g->n_models > 1) return fail(DARTRAY_E_INVAL, "maps are made of single-model grids");
     int rc = set_device(g);
     if (rc) return rc;
     const long long npix = 12ll << (2 * nside_k);
@@ -1156,6 +1599,7 @@ int dartray_map_noalloc(dartray_grid *g, const double observer[3], int32_t nside
     g_last_error.clear();
     if (!g || !observer || !map) return fail(DARTRAY_E_INVAL, "null argument");
     if (nside_k < 0 || nside_k > 10 || max_sub < 0 || max_sub > 6) return fail(DARTRAY_E_INVAL, "bad map size");
+    if (g->n_models > 1) return fail(DARTRAY_E_INVAL, "maps are made of single-model grids");
     const long long npix = 12ll << (2 * nside_k);
     const long long nmap = npix * g->nl;
     if (nmap > kNoAllocMapFloats) {
@@ -1192,6 +1636,7 @@ int dartray_map_noalloc(dartray_grid *g, const double observer[3], int32_t nside
 int dartray_state_save(dartray_grid *g, const char *path) {
     g_last_error.clear();
     if (!g || !path) return fail(DARTRAY_E_INVAL, "null argument");
+    if (g->n_models > 1) return fail(DARTRAY_E_INVAL, "state files hold single-model grids");
     int rc = set_device(g);
     if (rc) return rc;
     const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
@@ -1219,6 +1664,7 @@ int dartray_state_save(dartray_grid *g, const char *path) {
 int dartray_state_load(dartray_grid *g, const char *path) {
     g_last_error.clear();
     if (!g || !path) return fail(DARTRAY_E_INVAL, "null argument");
+    if (g->n_models > 1) return fail(DARTRAY_E_INVAL, "state files hold single-model grids");
     int rc = set_device(g);
     if (rc) return rc;
     const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
@@ -1250,6 +1696,36 @@ int dartray_state_load(dartray_grid *g, const char *path) {
     if (!ok) return fail(DARTRAY_E_INVAL, "truncated state file");
     g->l_sca2 = l2;
     g->have_direct = hdr[3] != 0;
+    return DARTRAY_OK;
+}
+
+int dartray_model_info(const dartray_grid *g, int32_t model, int64_t *leaf_offset, int32_t *n_leaf,
+                       int64_t *point_offset, double *remaining_frac, int32_t *active) {
+    if (!g || model < 0 || model >= g->n_models) return fail(DARTRAY_E_INVAL, "bad model index");
+    if (leaf_offset) *leaf_offset = g->m_leaf0[model];
+    if (n_leaf) *n_leaf = g->m_nleaf[model];
+    if (point_offset) *point_offset = g->m_point0[model];
+    if (remaining_frac) *remaining_frac = g->m_rem[model];
+    if (active) *active = g->m_active[model];
+    return DARTRAY_OK;
+}
+
+int dartray_model_stats(const dartray_grid *g, int32_t model, dartray_stats *st) {
+    if (!g || !st || model < 0 || model >= g->n_models) return fail(DARTRAY_E_INVAL, "bad argument");
+    std::memset(st, 0, sizeof *st);
+    const double *L = &g->m_ledger[static_cast<size_t>(model) * LG_N * g->nl];
+    for (int l = 0; l < g->nl; ++l) {
+        const double w = g->G.albedo[l];
+        st->emitted[l] = L[LG_EMITTED * g->nl + l];
+        st->absorbed[l] = (1.0 - w) * L[LG_DEPOSITED * g->nl + l];
+        st->scattered[l] = w * L[LG_DEPOSITED * g->nl + l];
+        st->escaped[l] = L[LG_ESCAPED * g->nl + l];
+        st->blocked[l] = L[LG_BLOCKED * g->nl + l];
+        st->cut[l] = L[LG_CUT * g->nl + l];
+        st->skipped[l] = L[LG_SKIPPED * g->nl + l];
+    }
+    st->f_u = g->m_fu[model];
+    st->l_sca2 = g->m_lsca2[model];
     return DARTRAY_OK;
 }
 

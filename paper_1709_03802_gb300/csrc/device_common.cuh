@@ -18,6 +18,16 @@ constexpr int kDirTabLevels = 11;
 __host__ __device__ inline int64_t dir_tab_offset(int k) { return 4 * ((int64_t(1) << (2 * k)) - 1); }
 
 // ------------------------------------------------------------------ grid
+// One model of a batched grid: its root lattice (roots are nodes node0 ..
+// node0 + nroot[0]*nroot[1]*nroot[2] - 1) and its step-1 radius.
+struct ModelDev {
+    int nroot[3];
+    float root_lo[3];
+    float root_size;
+    int node0;
+    float r_pre;
+};
+
 struct DevGrid {
     int nroot[3];
     float root_lo[3];
@@ -37,14 +47,43 @@ struct DevGrid {
     float albedo[kMaxLambda], g[kMaxLambda];
     int k_lam[kMaxLambda];
     long long off_lam[kMaxLambda];
+    // octant mode (symmetric models): only sources in the first octant are
+    // traced and every deposit is also made, reflected, in the seven images
+    // of its cell about the planes through the model centre
+    int octant;
+    float centre[3];
+    const int32_t *mirror;        // [7][n_leaf]: image of a leaf under reflection mask 1..7
+    const int32_t *mirror_pix;    // [7][kMirrorPix]: image of a j_sca pixel (levels 0..3, table order)
+    // batched grids: several independent models in one forest, each with its
+    // own root lattice; rays never leave their model (face links end at its
+    // boundary)
+    int n_models;
+    const ModelDev *models;       // [n_models]
+    const uint16_t *leaf_model;   // [n_leaf] model of each leaf (batched grids only)
+    const uint16_t *point_model;  // [n_point] model of each point source (batched grids only)
 };
+
+__device__ __forceinline__ int model_of_leaf(const DevGrid &G, int leaf) {
+    return G.n_models > 1 ? static_cast<int>(__ldg(&G.leaf_model[leaf])) : 0;
+}
+
+constexpr int kMirrorPix = 1020;  // pixel centres of levels 0..3
+
+// image of leaf c under reflection mask m (0: the leaf itself)
+__device__ __forceinline__ int mirror_leaf(const DevGrid &G, int m, int c) {
+    return m == 0 ? c : __ldg(&G.mirror[static_cast<long long>(m - 1) * G.n_leaf + c]);
+}
+// image of pixel q of j_sca level k under reflection mask m
+__device__ __forceinline__ int mirror_pixel(const DevGrid &G, int m, int k, int q) {
+    return m == 0 ? q : __ldg(&G.mirror_pix[(m - 1) * kMirrorPix + dir_tab_offset(k) + q]);
+}
 
 // ------------------------------------------------------------------ HEALPix
 // Face f: ring index (from the north pole) of pixel (ix, iy) is
 // kFaceRow[f]*nside - ix - iy - 1; the face centre sits at longitude
 // kFaceLon[f]*pi/4.
-__device__ __constant__ int kFaceRow[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
-__device__ __constant__ int kFaceLon[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};
+static __device__ __constant__ int kFaceRow[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
+static __device__ __constant__ int kFaceLon[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};
 
 __device__ inline uint32_t compact_bits(uint64_t v) {
     v &= 0x5555555555555555ull;
@@ -166,7 +205,7 @@ __device__ inline uint64_t vec2pix_d(int k, double vx, double vy, double vz) {
 
 // Directions beyond the table (levels above kDirTabLevels; rare), kept out of
 // line so the marcher's code stays small.
-__device__ __noinline__ float3 ray_dir_computed(int k, uint64_t p) {
+static __device__ __noinline__ float3 ray_dir_computed(int k, uint64_t p) {
     double v[3];
     pix2vec_d(k, p, v);
     return make_float3(static_cast<float>(v[0]), static_cast<float>(v[1]), static_cast<float>(v[2]));
@@ -223,7 +262,23 @@ __device__ inline int descend(const DevGrid &G, int node, float4 b, const float3
     return -c - 1;
 }
 
-__device__ inline int locate_root(const DevGrid &G, const float3 p, const float3 n) {
+// Leaf of model `model` of a batched grid holding p (-1 outside the model);
+// out of line, so that single-model traversal code stays small.
+static __device__ __noinline__ int locate_root_model(const DevGrid &G, int model, const float3 p, const float3 n) {
+    const ModelDev &M = G.models[model];
+    const int ix = root_index(p.x, M.root_lo[0], M.root_size, M.nroot[0], n.x);
+    const int iy = root_index(p.y, M.root_lo[1], M.root_size, M.nroot[1], n.y);
+    const int iz = root_index(p.z, M.root_lo[2], M.root_size, M.nroot[2], n.z);
+    if (ix < 0 || iy < 0 || iz < 0) return -1;
+    const int node = M.node0 + ix + M.nroot[0] * (iy + M.nroot[1] * iz);
+    const float4 b = make_float4(M.root_lo[0] + float(ix) * M.root_size, M.root_lo[1] + float(iy) * M.root_size,
+                                 M.root_lo[2] + float(iz) * M.root_size, M.root_size);
+    return descend(G, node, b, p, n);
+}
+
+// Leaf of model `model` holding p (-1 outside the model).
+__device__ inline int locate_root(const DevGrid &G, int model, const float3 p, const float3 n) {
+    if (G.n_models > 1) return locate_root_model(G, model, p, n);
     const int ix = root_index(p.x, G.root_lo[0], G.root_size, G.nroot[0], n.x);
     const int iy = root_index(p.y, G.root_lo[1], G.root_size, G.nroot[1], n.y);
     const int iz = root_index(p.z, G.root_lo[2], G.root_size, G.nroot[2], n.z);
@@ -248,8 +303,8 @@ constexpr int kLinkSameSize = -(1 << 30);
 // the leaf holding the exit point pe.  When the link leads straight to a leaf
 // its box is returned in *box (computed for a same-size neighbour) and
 // *has_box is set.
-__device__ inline int follow_link(const DevGrid &G, int code, int a, const float4 cur, const float3 pe,
-                                  const float3 n, float4 *box, bool *has_box) {
+__device__ inline int follow_link(const DevGrid &G, int code, int a, int cur_leaf, const float4 cur,
+                                  const float3 pe, const float3 n, float4 *box, bool *has_box) {
     *has_box = false;
     if (code == -1) return -1;
     if (code < 0) {
@@ -272,11 +327,11 @@ __device__ inline int follow_link(const DevGrid &G, int code, int a, const float
             *has_box = true;
             return lf;
         }
-        return locate_root(G, pe, n);
+        return locate_root(G, model_of_leaf(G, cur_leaf), pe, n);
     }
     const float4 b = __ldg(&G.node_box[code]);
     if (inside_box(b, pe, n)) return descend(G, code, b, pe, n);
-    return locate_root(G, pe, n);
+    return locate_root(G, model_of_leaf(G, cur_leaf), pe, n);
 }
 
 __device__ inline int next_leaf(const DevGrid &G, int leaf, int tie, const float3 pe, const float3 n) {
@@ -285,7 +340,7 @@ __device__ inline int next_leaf(const DevGrid &G, int leaf, int tie, const float
     const int code = __ldg(&G.leaf_rope[6 * leaf + 2 * a + (na > 0.f ? 1 : 0)]);
     float4 b;
     bool hb;
-    return follow_link(G, code, a, __ldg(&G.leaf_box[leaf]), pe, n, &b, &hb);
+    return follow_link(G, code, a, leaf, __ldg(&G.leaf_box[leaf]), pe, n, &b, &hb);
 }
 
 // Reciprocal square root of the Henyey-Greenstein weights (Eq. 4): the
@@ -299,6 +354,35 @@ __device__ __forceinline__ float hg_rsqrt(float t) {
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
     return r;
 }
+
+// ------------------------------------------------------- fixed-point sums
+// Deterministic mode: a non-negative value v is accumulated as the integer
+// round(v 2^e) in 64 bits.  Integer additions commute and associate, so the
+// sums, and everything computed from them, do not depend on the order in
+// which threads add.  Exponents are chosen per cell and wavelength so that
+// an upper bound of the cell's total maps to at most 2^60.  The scaling by
+// 2^e is exact (two powers of two, each a normal float).
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+__device__ __forceinline__ unsigned long long to_fix(float v, int e) {
+    const int e1 = e / 2;
+    return __float2ull_rn(v * pow2f(e1) * pow2f(e - e1));
+}
+// ceil(log2(x)) for a positive normal float, exact
+__device__ __forceinline__ int ceil_log2f(float x) {
+    int e;
+    const float f = frexpf(x, &e);  // x = f 2^e, f in [0.5, 1)
+    return f == 0.5f ? e - 1 : e;
+}
+// exponent of the j_sca fixed point of a cell with extinction kr and side L:
+// its pixels receive at most 4 L_emit min(1, 2 kr L) (eJ_base covers 4 L_emit)
+__device__ __forceinline__ int cell_exp_jsca(int eJ_base, float kr, float L) {
+    const float x = fminf(1.f, 2.f * kr * L);
+    return eJ_base - (x > 0.f ? ceil_log2f(x) : 0);
+}
+// exponent of the U fixed point of a cell of side L (a power of two): the
+// cell receives at most 4 sqrt(3) L_emit / (L^2 c) (eU_base covers the
+// factor without L^-2)
+__device__ __forceinline__ int cell_exp_u(int eU_base, float L) { return eU_base + 2 * ilogbf(L); }
 
 // ------------------------------------------------------------------ rays
 enum RayKind : int { kSeed = 0, kChild = 1, kMerged = 2, kResumed = 3 };
@@ -326,11 +410,12 @@ __device__ __host__ inline unsigned rr_meta(int lev, int kind, int axis) {
 // ledger slots (luminosities) and counters
 enum { LG_EMITTED = 0, LG_DEPOSITED, LG_ESCAPED, LG_BLOCKED, LG_CUT, LG_SKIPPED, LG_N };
 enum { CT_RAYS = 0, CT_CROSS, CT_SPLIT, CT_MERGE, CT_BLOCK, CT_ESCAPE, CT_CUT, CT_LOW, CT_RESUME,
-       CT_WAVES, CT_SOURCES, CT_JPIX, CT_FLUSH, CT_N };
+       CT_WAVES, CT_SOURCES, CT_JPIX, CT_FLUSH, CT_REC, CT_N };
 
 struct DevStats {
     double ledger[LG_N][kMaxLambda];
     unsigned long long cnt[CT_N];
+    unsigned long long ledger_fix[LG_N][kMaxLambda];  // deterministic mode (fixed point, exponent eL)
 };
 
 // device status word

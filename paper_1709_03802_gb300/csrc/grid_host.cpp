@@ -192,4 +192,40 @@ std::string build_topology(const int32_t nroot[3], const double root_lo[3], doub
     return "";
 }
 
+std::string build_mirrors(const int32_t nroot[3], const double root_lo[3], double root_size,
+                          const int32_t *first_child, const int32_t *leaf_of_node, const HostTopo &t,
+                          std::vector<int32_t> *mirror) {
+    const int64_t n_leaf = static_cast<int64_t>(t.leaf_box.size() / 4);
+    double centre[3];
+    for (int a = 0; a < 3; ++a) centre[a] = root_lo[a] + 0.5 * nroot[a] * root_size;
+    Walker w{nroot, root_lo, root_size, first_child};
+    mirror->assign(static_cast<size_t>(7) * n_leaf, -1);
+    char msg[256];
+    for (int64_t lf = 0; lf < n_leaf; ++lf) {
+        const float *b = &t.leaf_box[4 * lf];
+        for (int m = 1; m < 8; ++m) {
+            double lo[3], q[3];
+            const int s[3] = {1, 1, 1};
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = ((m >> a) & 1) ? 2.0 * centre[a] - static_cast<double>(b[a]) - b[3] : static_cast<double>(b[a]);
+                q[a] = lo[a] + 0.5 * b[3];
+            }
+            const int64_t nd = w.find(q, s, b[3]);
+            const bool ok = nd >= 0 && first_child[nd] < 0 && t.node_box[4 * nd + 3] == b[3] &&
+                            t.node_box[4 * nd] == static_cast<float>(lo[0]) &&
+                            t.node_box[4 * nd + 1] == static_cast<float>(lo[1]) &&
+                            t.node_box[4 * nd + 2] == static_cast<float>(lo[2]);
+            if (!ok) {
+                std::snprintf(msg, sizeof msg,
+                              "grid is not mirror-symmetric about its centre (leaf %lld has no image under "
+                              "reflection mask %d)",
+                              static_cast<long long>(lf), m);
+                return msg;
+            }
+            (*mirror)[static_cast<size_t>(m - 1) * n_leaf + lf] = leaf_of_node[nd];
+        }
+    }
+    return "";
+}
+
 }  // namespace dartray

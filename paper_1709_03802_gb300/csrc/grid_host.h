@@ -33,4 +33,12 @@ std::string build_topology(const int32_t nroot[3], const double root_lo[3], doub
                            int32_t n_nodes, int32_t n_leaf, const int32_t *first_child,
                            const int32_t *leaf_of_node, HostTopo *t);
 
+// Octant mode: the images of every leaf under the seven reflections about
+// the planes through the model centre (reflection mask m = bit a set: axis a
+// flipped), mirror[(m - 1) * n_leaf + leaf].  Returns "" on success, else a
+// message naming a leaf without an image (the grid is not mirror-symmetric).
+std::string build_mirrors(const int32_t nroot[3], const double root_lo[3], double root_size,
+                          const int32_t *first_child, const int32_t *leaf_of_node, const HostTopo &t,
+                          std::vector<int32_t> *mirror);
+
 }  // namespace dartray

@@ -26,7 +26,7 @@ __device__ inline void tau_to_observer(const DevGrid &G, const float3 x, const f
     const float dist = sqrtf(n.x * n.x + n.y * n.y + n.z * n.z);
     if (!(dist > 0.f)) return;
     n = make_float3(n.x / dist, n.y / dist, n.z / dist);
-    int leaf = locate_root(G, x, n);
+    int leaf = locate_root(G, 0, x, n);  // maps are made of single-model grids
     float d = 0.f;
     const float inf = __int_as_float(0x7f800000);
     for (int guard = 0; leaf >= 0 && guard < (1 << 22); ++guard) {

@@ -42,7 +42,7 @@ class dartray_params(C.Structure):
                 ("merge", C.c_int32), ("max_cross", C.c_int32), ("max_waves", C.c_int32),
                 ("src_stride", C.c_int32), ("src_offset", C.c_int32), ("queue_rays", C.c_int64),
                 ("src_batch", C.c_int64), ("profile", C.c_int32), ("deposit_direct", C.c_int32),
-                ("deposit_records", C.c_int64)]
+                ("deposit_records", C.c_int64), ("deterministic", C.c_int32), ("octant", C.c_int32)]
 
 
 _L = MAX_LAMBDA
@@ -57,7 +57,7 @@ class dartray_stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("march_ms", C.c_double), ("march_launches", C.c_int64),
                 ("jsca_pixels", C.c_int64), ("flush_ms", C.c_double), ("busy_ms", C.c_double),
                ("restarts", C.c_int64), ("march_sum_ms", C.c_double), ("flushes", C.c_int64),
-               ("batches", C.c_int64)]
+               ("batches", C.c_int64), ("records", C.c_int64)]
 
     def to_dict(self, n_lambda=1):
         out = {}
@@ -97,6 +97,9 @@ def load(build_if_missing=True):
         "dartray_map": ([P, P, C.c_int32, C.c_int32, C.c_int32, P, C.c_int], C.c_int),
         "dartray_map_noalloc": ([P, P, C.c_int32, C.c_int32, C.c_int32, P, C.c_int], C.c_int),
         "dartray_state_save": ([P, C.c_char_p], C.c_int),
+        "dartray_grid_create_batch": ([P, C.c_int32, P, P, P], C.c_int),
+        "dartray_model_info": ([P, C.c_int32, P, P, P, P, P], C.c_int),
+        "dartray_model_stats": ([P, C.c_int32, P], C.c_int),
         "dartray_state_load": ([P, C.c_char_p], C.c_int),
         "dartray_grid_destroy": ([P], None),
         "dartray_last_error": ([], C.c_char_p),
@@ -111,7 +114,8 @@ def load(build_if_missing=True):
 
 EXPORTED = ("dartray_params_default", "dartray_grid_create", "dartray_direct", "dartray_scatter_iter",
             "dartray_rfed", "dartray_jsca_layout", "dartray_jsca", "dartray_map", "dartray_map_noalloc",
-            "dartray_state_save", "dartray_state_load", "dartray_grid_destroy", "dartray_last_error")
+            "dartray_state_save", "dartray_state_load", "dartray_grid_destroy", "dartray_last_error",
+            "dartray_grid_create_batch", "dartray_model_info", "dartray_model_stats")
 
 
 def _check(rc):
@@ -132,6 +136,30 @@ def dartray_grid_create(desc, params, stream=None):
     _check(load().dartray_grid_create(C.byref(desc), C.byref(params) if params is not None else None,
                                       C.c_void_p(stream or 0), C.byref(h)))
     return h
+
+
+def dartray_grid_create_batch(descs, params, stream=None):
+    arr = (dartray_grid_desc * len(descs))(*descs)
+    h = C.c_void_p()
+    _check(load().dartray_grid_create_batch(arr, len(descs), C.byref(params) if params is not None else None,
+                                            C.c_void_p(stream or 0), C.byref(h)))
+    return h
+
+
+def dartray_model_info(h, model):
+    l0, p0 = C.c_int64(), C.c_int64()
+    nl, act = C.c_int32(), C.c_int32()
+    rem = C.c_double()
+    _check(load().dartray_model_info(h, int(model), C.byref(l0), C.byref(nl), C.byref(p0), C.byref(rem),
+                                     C.byref(act)))
+    return dict(leaf_offset=l0.value, n_leaf=nl.value, point_offset=p0.value, remaining=rem.value,
+                active=bool(act.value))
+
+
+def dartray_model_stats(h, model):
+    st = dartray_stats()
+    _check(load().dartray_model_stats(h, int(model), C.byref(st)))
+    return st
 
 
 def dartray_direct(h):
@@ -211,6 +239,45 @@ def default_params(**overrides):
     return p
 
 
+def grid_desc(grid):
+    """dartray_grid_desc of a synth.Grid-like object, and the arrays it points
+    to (keep them alive while the description is used)."""
+    fields = dict(first_child=grid.first_child, leaf_of_node=grid.leaf_of_node, kappa_rho=grid.kappa_rho,
+                  emissivity=grid.emissivity, albedo=grid.albedo, g=grid.g, point_xyz=grid.point_xyz,
+                  point_lum=grid.point_lum)
+    on_dev = _is_cuda_tensor(grid.kappa_rho)
+    keep = {}
+    for k, v in fields.items():
+        if on_dev:
+            keep[k] = v.contiguous()
+        else:
+            dt = np.int32 if k in ("first_child", "leaf_of_node") else np.float32
+            keep[k] = np.ascontiguousarray(v, dt)
+    d = dartray_grid_desc()
+    d.nroot[:] = [int(v) for v in grid.nroot]
+    d.root_lo[:] = [float(v) for v in grid.root_lo]
+    d.root_size = float(grid.root_size)
+    d.n_nodes = int(keep["first_child"].shape[0])
+    d.n_leaf = int(grid.n_leaf)
+    d.n_lambda = int(grid.n_lambda)
+    for k in fields:
+        setattr(d, k, _ptr(keep[k]).value if _ptr(keep[k]) is not None else None)
+    d.n_point = int(keep["point_xyz"].shape[0])
+    d.inputs_on_device = 1 if on_dev else 0
+    return d, keep
+
+
+def _default_stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            stream = None
+    return stream
+
+
 class DartRay:
     """One grid on the current CUDA device.
 
@@ -225,38 +292,9 @@ class DartRay:
         self.n_leaf = int(grid.n_leaf)
         self.n_lambda = int(grid.n_lambda)
         self.params = default_params(**params)
-        fields = dict(first_child=grid.first_child, leaf_of_node=grid.leaf_of_node, kappa_rho=grid.kappa_rho,
-                      emissivity=grid.emissivity, albedo=grid.albedo, g=grid.g, point_xyz=grid.point_xyz,
-                      point_lum=grid.point_lum)
-        on_dev = _is_cuda_tensor(grid.kappa_rho)
-        keep = {}
-        for k, v in fields.items():
-            if on_dev:
-                keep[k] = v.contiguous()
-            else:
-                dt = np.int32 if k in ("first_child", "leaf_of_node") else np.float32
-                keep[k] = np.ascontiguousarray(v, dt)
-        self._keep = keep
-        d = dartray_grid_desc()
-        d.nroot[:] = [int(v) for v in grid.nroot]
-        d.root_lo[:] = [float(v) for v in grid.root_lo]
-        d.root_size = float(grid.root_size)
-        d.n_nodes = int(keep["first_child"].shape[0])
-        d.n_leaf = self.n_leaf
-        d.n_lambda = self.n_lambda
-        for k in fields:
-            setattr(d, k, _ptr(keep[k]).value if _ptr(keep[k]) is not None else None)
-        d.n_point = int(keep["point_xyz"].shape[0])
-        d.inputs_on_device = 1 if on_dev else 0
-        if stream is None:
-            try:
-                import torch
-                if torch.cuda.is_available():
-                    stream = torch.cuda.current_stream().cuda_stream
-            except ImportError:
-                stream = None
-        self.stream = stream
-        self._h = dartray_grid_create(d, self.params, stream)
+        d, self._keep = grid_desc(grid)
+        self.stream = _default_stream(stream)
+        self._h = dartray_grid_create(d, self.params, self.stream)
         self.k_lam, self.off_lam, self.sca_len = dartray_jsca_layout(self._h, self.n_lambda)
 
     def close(self):
@@ -312,3 +350,44 @@ class DartRay:
 
     def load(self, path):
         dartray_state_load(self._h, path)
+
+
+class DartRayBatch(DartRay):
+    """Several models traced together in one grid (dartray_grid_create_batch).
+
+    ``grids`` share n_lambda, albedo and g.  rfed() and jsca() return all
+    models concatenated; model_rfed(m), model_jsca_block(m, l) and
+    model_stats(m) return one model's part."""
+
+    def __init__(self, grids, stream=None, **params):
+        self.grids = list(grids)
+        self.grid = self.grids[0]
+        self.n_leaf = int(sum(g.n_leaf for g in self.grids))
+        self.n_lambda = int(self.grid.n_lambda)
+        self.params = default_params(**params)
+        descs, self._keep = [], []
+        for g in self.grids:
+            d, k = grid_desc(g)
+            descs.append(d)
+            self._keep.append(k)
+        self.stream = _default_stream(stream)
+        self._h = dartray_grid_create_batch(descs, self.params, self.stream)
+        self.k_lam, self.off_lam, self.sca_len = dartray_jsca_layout(self._h, self.n_lambda)
+        self.info = [dartray_model_info(self._h, m) for m in range(len(self.grids))]
+
+    def model_info(self, m):
+        return dartray_model_info(self._h, m)
+
+    def model_stats(self, m):
+        return dartray_model_stats(self._h, m).to_dict(self.n_lambda)
+
+    def model_rfed(self, m, U=None, L_abs=None):
+        U, L_abs = self.rfed()
+        a = self.info[m]["leaf_offset"]
+        b = a + self.info[m]["n_leaf"]
+        return U[a:b], L_abs[a:b]
+
+    def model_jsca_block(self, m, l, which="total"):
+        blk = self.jsca_block(l, which)
+        a = self.info[m]["leaf_offset"]
+        return blk[a:a + self.info[m]["n_leaf"]]

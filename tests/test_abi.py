@@ -135,3 +135,17 @@ def test_binding_structs_match_the_header_layout(cls, tmp_path):
     size, offsets = _c_layout(cls.__name__, fields, tmp_path)
     assert C.sizeof(cls) == size
     assert [getattr(cls, f).offset for f in fields] == offsets
+
+
+def test_octant_mode_rejects_an_asymmetric_model():
+    """The octant mode needs a model symmetric about its centre: config 1's
+    source sits off the centre, so the grid is refused before any device
+    work."""
+    grid = synth.config1()
+    d, keep = _desc(grid)
+    p = pkg.dartray_params_default()
+    p.octant = 1
+    lib = pkg.load()
+    h = C.c_void_p()
+    rc = lib.dartray_grid_create(C.byref(d), C.byref(p), None, C.byref(h))
+    assert rc == -1 and "octant" in lib.dartray_last_error().decode()

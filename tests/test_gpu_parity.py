@@ -377,3 +377,33 @@ def test_galaxy_full_size_small_buffers():
     st = gpu.direct_stats
     assert st["restarts"] > 0 and st["flushes"] > 1 and st["batches"] > 1, st
     assert gpu.last_stats["flushes"] > 1
+
+
+def test_deterministic_mode_bit_identical_and_within_tolerance():
+    """deterministic=1 sums U, the j_sca rows and the ledger in 64-bit fixed
+    point: two runs give bit-identical RFED, scattering source function,
+    ledger and counters, and both match the oracle at the usual tolerances.
+    The galaxy (merges, splits, blocking, several batches) is run on sampled
+    sources."""
+    grid = synth.galaxy_disk(max_level=3, threshold=0.3, nroot=(3, 3, 1), root_size=4.0)
+    params = dict(a_rt=0.05, r_pre=2.0, src_stride=23, deterministic=1)
+    gpu, ref = run_pair(grid, 1, **params)
+    again = DartRay(grid, **params)
+    s1 = again.direct()
+    for k in ("crossings", "rays", "splits", "merges", "blocks", "escapes", "records", "emitted", "absorbed",
+              "scattered", "escaped", "blocked", "skipped"):
+        assert np.array_equal(np.asarray(s1[k]), np.asarray(gpu.direct_stats[k])), k
+    rem_a, s2 = again.scatter_iter()
+    for k in ("crossings", "rays", "splits", "merges", "blocks", "escapes", "absorbed", "scattered", "escaped"):
+        assert np.array_equal(np.asarray(s2[k]), np.asarray(gpu.last_stats[k])), k
+    assert np.array_equal(again.rfed()[0], gpu.rfed()[0])
+    assert np.array_equal(again.jsca("total"), gpu.jsca("total"))
+    assert np.array_equal(again.jsca("pending"), gpu.jsca("pending"))
+
+
+def test_deterministic_mode_galaxy_full_size():
+    """The 297,840-leaf galaxy in the deterministic mode on sampled sources,
+    against the oracle, with the benchmark's launch configuration."""
+    grid = synth.config2()
+    params = dict(a_rt=0.05, r_pre=0.15 * grid.model_size, src_stride=30000, deterministic=1)
+    run_pair(grid, 1, **params)
