@@ -168,6 +168,116 @@ def run_step(gpu, grid):
                 iters=it, iter_ms=it_ms, launches=launches, map=m)
 
 
+# ---------------------------------------------------------------- batched forms
+CUBES = 32
+
+
+def cube_models():
+    """The clumpy cubes of the batched workload: 32 lognormal cubes
+    (sigma_ln rho = 1, seeded), N_i = round(16 * 4^(i/31)) cells a side
+    (16^3 to 64^3), cell side 1/16 kpc, mean edge-to-edge optical depth
+    log-spaced from 0.5 to 5, 16 emitting cells each drawn with probability
+    proportional to the density."""
+    import synth
+    out = []
+    for i in range(CUBES):
+        n = int(round(16 * 4 ** (i / (CUBES - 1))))
+        tau = 0.5 * 10 ** (i / (CUBES - 1))
+        out.append(synth.lognormal_cube(n, 100 + i, tau_mean=tau, n_src=16, box_size=n / 16.0))
+    return out
+
+
+def galaxy_8_lambda():
+    """The galaxy at 8 wavelengths log-spaced 0.15-2.2 um: kappa ~ lambda^-1.3
+    (tau_B = 2 at 0.443 um), albedo 0.7 -> 0.4 and g 0.75 -> 0.4 linear in
+    log lambda (k_lambda from 3 down to 1), the stellar emissivity the same
+    at every wavelength."""
+    import synth
+    g = synth.config2()
+    lam = np.geomspace(0.15, 2.2, 8)
+    t = np.log(lam / lam[0]) / np.log(lam[-1] / lam[0])
+    kr = g.kappa_rho * (lam / 0.443) ** -1.3
+    em = np.repeat(g.emissivity, 8, axis=1)
+    return g.with_lambda(kr, em, 0.7 - 0.3 * t, 0.75 - 0.35 * t), lam
+
+
+def timed_call(f):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = f()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def bench_batched(params):
+    """The batched form against the plain loop on the same GPU.
+
+    models: the 32 cubes traced together in one grid (steps 1-2) against a
+    loop that traces them one grid at a time; wavelengths: the galaxy at 8
+    wavelengths in one grid (rays carry all 8) against 8 single-wavelength
+    grids, steps 1-2 and one scattering iteration on every 64th source.
+    Times cover the sweep calls (grids are created before), and both forms
+    are compared cell by cell."""
+    from paper_1709_03802_gb300 import DartRay, DartRayBatch
+    p = dict(a_rt=params["a_rt"], n_rays_min=5, n_rays_max=40, k0=2, merge=1, r_pre=-1.0)
+    out = {}
+    # --- models
+    cubes = cube_models()
+    plain_s, plain_c, plain_U = 0.0, 0, []
+    for c in cubes:
+        g = DartRay(c, **p)
+        st, dt = timed_call(g.direct)
+        plain_s += dt
+        plain_c += st["crossings"]
+        plain_U.append(g.rfed()[0][:, 0].copy())
+        g.close()
+    b = DartRayBatch(cubes, **p)
+    choice, trial_ms = b.autotune(sample_stride=4)
+    st, batched_s = timed_call(b.direct)
+    worst = 0.0
+    for m, U1 in enumerate(plain_U):
+        U = b.model_rfed(m)[0][:, 0]
+        big = U1 > 1e-6 * U1.max()
+        worst = max(worst, float(np.abs(U[big] / U1[big] - 1).max()))
+    b.close()
+    out["models"] = {"workload": f"{CUBES} lognormal cubes 16^3-64^3 ({sum(c.n_leaf for c in cubes)} leaves), "
+                                 "16 emitting cells each, steps 1-2",
+                     "plain_loop_s": plain_s, "batched_s": batched_s, "speedup": plain_s / batched_s,
+                     "crossings": int(st["crossings"]), "plain_crossings": int(plain_c),
+                     "batched_crossings_per_s": st["crossings"] / batched_s,
+                     "max_rel_diff_U": worst, "autotune_choice": ["deferred", "deferred, 1/16 buffer", "atomic"][choice],
+                     "autotune_ms": trial_ms}
+    # --- wavelengths
+    g8, lam = galaxy_8_lambda()
+    cap = dict(queue_rays=1 << 25, deposit_records=1 << 26, src_stride=64)
+    one = DartRay(g8, **p, **cap)
+
+    def sweep8():
+        s1 = one.direct()
+        _, s2 = one.scatter_iter()
+        return s1["crossings"] + s2["crossings"]
+
+    c8, t8 = timed_call(sweep8)
+    U8 = one.rfed()[0].copy()
+    one.close()
+    t1, worst = 0.0, 0.0
+    for l in range(8):
+        gl = g8.with_lambda(g8.kappa_rho[:, l:l + 1], g8.emissivity[:, l:l + 1], g8.albedo[l:l + 1], g8.g[l:l + 1])
+        gg = DartRay(gl, **p, **cap)
+        _, dt = timed_call(lambda: (gg.direct(), gg.scatter_iter()))
+        t1 += dt
+        U1 = gg.rfed()[0][:, 0]
+        big = U1 > 1e-6 * U1.max()
+        worst = max(worst, float(np.abs(U8[big, l] / U1[big] - 1).max()))
+        gg.close()
+    out["wavelengths"] = {"workload": "galaxy at 8 wavelengths 0.15-2.2 um, every 64th source, steps 1-2 + one "
+                                      "scattering iteration",
+                          "plain_loop_s": t1, "batched_s": t8, "speedup": t1 / t8, "crossings": int(c8),
+                          "max_rel_diff_U": worst}
+    return out
+
+
 def cpu_sample(grid, params, stride, offset=0):
     import oracle
     p = oracle.OracleParams(**{k: v for k, v in params.items() if k in oracle.OracleParams.__dataclass_fields__},
@@ -222,6 +332,7 @@ def main():
     ap.add_argument("--src-stride", type=int, default=1,
                     help="profiling aid: trace every n-th primary source only (default: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparisons")
     # capacities (0 = automatic); results do not depend on them.  Smaller
     # buffers keep the device footprint of a profiling run to a few GB.
     ap.add_argument("--queue-rays", type=int, default=0)
@@ -355,6 +466,9 @@ def main():
                 "deposit_flush_share_of_step": (sum(r["flush_ms"] for r in results) / total_ms
                                                 if total_ms else None)}
     gpu.close()
+    batched = None
+    if not args.no_batched and args.src_stride == 1:
+        batched = bench_batched(params)
 
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.src_stride == 1:
@@ -372,7 +486,8 @@ def main():
                 "crossings_per_step": cross,
                 "deposit_records_per_step": float(np.mean([r["records"] for r in results])),
                 "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
-                "gpu_launches": int(sum(r["launches"] for r in results)), "clocks": clocks}
+                "gpu_launches": int(sum(r["launches"] for r in results)), "clocks": clocks,
+                "batched_vs_plain": batched}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

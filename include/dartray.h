@@ -127,6 +127,9 @@ typedef struct dartray_params {
                                 as the full mode; counters count the rays traced.  Requires
                                 src_stride 1; a grid that is not symmetric is rejected with
                                 DARTRAY_E_INVAL (0) */
+    int32_t graphs;          /* 1: each pipeline's rounds of waves (ray march, merge, deposit
+                                flush, wave advance) are captured once per phase as a CUDA
+                                graph and replayed; ignored with profile = 1 (1) */
 } dartray_params;
 
 /* Per-call statistics.  Ledger entries are luminosities per wavelength of the
@@ -232,6 +235,60 @@ int dartray_direct(dartray_grid *grid, dartray_stats *stats);
  * step 2); callers stop once it is below f_L.  Errors: STATE (no dartray_direct
  * yet), LIMIT, QUEUE, CUDA. */
 int dartray_scatter_iter(dartray_grid *grid, double *remaining_frac, dartray_stats *stats);
+
+/*
+ * Dust emission and self-heating (Sect. 3.3).  The dust RT runs on a second
+ * grid with the same topology whose wavelengths are those of the dust
+ * emission (its kappa_rho, albedo and g are the dust's at those
+ * wavelengths).  dartray_dust_emission computes, per cell, the equilibrium
+ * temperature and emission of a synthetic modified blackbody (in place of
+ * grain models): the absorbed power
+ *   P = sum over both grids' wavelengths of (1 - albedo) kappa_rho c V U dlambda
+ * balances 4 pi V sum_i scale kabs_i B(lambda_i, T) dlambda_i with
+ * kabs_i = (1 - albedo_i) kappa_rho_i and B = lambda^-5 / (exp(c2/(lambda T)) - 1)
+ * (lambda in um, c2 = 14387.77 um K; T by bisection in [t_min, t_max]); the
+ * emission is j_i = scale kabs_i B(lambda_i, T).  The dust grid's
+ * emissivity becomes the change of j since the previous call (clipped at 0;
+ * the first call: j), which dartray_direct (first time) or
+ * dartray_direct_incremental (later) then propagates.  T [n_leaf] and j
+ * [n_leaf][n_lambda] (either may be NULL) go to host or device memory;
+ * *max_rel_change receives max |j - j_prev| / j_prev over cells and
+ * wavelengths with j_prev > 0 (infinite on the first call).  Iterate until
+ * it is below 1% (the paper's criterion).  Errors: INVAL, CUDA.
+ */
+typedef struct dartray_dust {
+    int32_t n_ir;                              /* = n_lambda of the dust grid */
+    double lam_ir[DARTRAY_MAX_LAMBDA];         /* dust wavelengths, um */
+    double dlam_ir[DARTRAY_MAX_LAMBDA];        /* their bin widths, um */
+    int32_t n_stellar;                         /* = n_lambda of the stellar grid */
+    double dlam_stellar[DARTRAY_MAX_LAMBDA];   /* stellar bin widths, um */
+    double scale;                              /* prefactor of the emission (model units) */
+    double t_min, t_max;                       /* temperature bracket, K */
+} dartray_dust;
+
+int dartray_dust_emission(dartray_grid *dust_grid, const dartray_grid *stellar_grid, const dartray_dust *dust,
+                          float *T, float *j, int dst_is_device, double *max_rel_change);
+
+/* Replace the emissivity [n_leaf][n_lambda] (host or device). */
+int dartray_set_emissivity(dartray_grid *grid, const float *emissivity, int src_is_device);
+
+/* Step 2 for the current emissivity on top of the present state (Sect. 3.3,
+ * items 5-6): no U_LL step (U_LL is the RFED of the previous call), U and
+ * the total j_sca keep their values and receive the new deposits; the
+ * pending j_sca starts from zero, and the following dartray_scatter_iter
+ * calls measure their remaining fraction against this step's scattered
+ * luminosity.  Errors: STATE (no dartray_direct yet), LIMIT, QUEUE, CUDA. */
+int dartray_direct_incremental(dartray_grid *grid, dartray_stats *stats);
+
+/* Autotuner: times steps 1 and 2 on every sample_stride-th source with each
+ * deposit schedule -- 0: deferred per-cell records in the full buffer, 1:
+ * deferred with a sixteenth of the buffer (smaller, more frequent flushes),
+ * 2: per-pixel atomics in the ray marcher -- and keeps the fastest for the
+ * later calls of the grid (results do not depend on the schedule).
+ * *choice receives its index and ms[3] the times (-1: not tried); either
+ * may be NULL.  The trial runs leave no state: call dartray_direct next.
+ * Errors: INVAL, and those of dartray_direct. */
+int dartray_autotune(dartray_grid *grid, int32_t sample_stride, int32_t *choice, double *ms);
 
 /* RFED U [n_leaf][n_lambda] and absorbed luminosity
  * L_abs = (1 - albedo) * kappa_rho * c_light * V * U [n_leaf][n_lambda]

@@ -789,8 +789,11 @@ static int or_mirrors(const or_grid *G, const double *leaf_box, const double cen
 }
 
 /* One phase of the sweep: mode 0 = step 1 (U_LL), 1 = step 2 (direct light),
- * 2 = one scattering iteration.  Returns 0 or a negative error. */
-static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode) {
+ * 2 = one scattering iteration.  keep_U (step 2 only): U starts from its
+ * current value instead of zero (the dust self-heating iterations of
+ * Sect. 3.3 process only the change of the dust emission).  Returns 0 or a
+ * negative error. */
+static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode, int keep_U) {
     const int nl = G->n_lambda;
     or_ctx C;
     memset(&C, 0, sizeof C);
@@ -811,7 +814,7 @@ static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode)
         memset(S->U_LL, 0, sizeof(double) * (size_t)G->n_leaf * nl);
         C.target = S->U_LL;
     } else {
-        if (mode == 1) memset(S->U, 0, sizeof(double) * (size_t)G->n_leaf * nl);
+        if (mode == 1 && !keep_U) memset(S->U, 0, sizeof(double) * (size_t)G->n_leaf * nl);
         C.target = S->U;
         memset(pend_nxt, 0, sizeof(double) * (size_t)S->sca_len);
         C.pend_dst = pend_nxt;
@@ -1020,15 +1023,25 @@ int or_direct(const or_grid *G, const or_params *P, or_state *S) {
     S->cur_is_a = 1;  /* deposits of step 2 go to pend_b (the "next" buffer) */
     memset(S->counters, 0, sizeof S->counters);  /* counters cover one call */
     memset(S->jsca_total, 0, sizeof(double) * (size_t)S->sca_len);
-    int rc = or_phase(G, P, S, 0);
+    int rc = or_phase(G, P, S, 0, 0);
     if (rc) return rc;
-    return or_phase(G, P, S, 1);
+    return or_phase(G, P, S, 1, 0);
+}
+
+/* Step 2 for the change of the dust emission in a self-heating iteration
+ * (Sect. 3.3, items 5-6): the emissivity holds that change; the U_LL step is
+ * skipped (U_LL equals the RFED of the previous iteration), U and the total
+ * j_sca start from their previous values. */
+int or_direct_incremental(const or_grid *G, const or_params *P, or_state *S) {
+    S->cur_is_a = 1;
+    memset(S->counters, 0, sizeof S->counters);
+    return or_phase(G, P, S, 1, 1);
 }
 
 /* One scattering iteration (Sect. 2); *remaining = pending / L_sca,2. */
 int or_scatter_iter(const or_grid *G, const or_params *P, or_state *S, double *remaining) {
     memset(S->counters, 0, sizeof S->counters);
-    int rc = or_phase(G, P, S, 2);
+    int rc = or_phase(G, P, S, 2, 0);
     if (rc) return rc;
     const double *nxt = S->cur_is_a ? S->pend_b : S->pend_a;
     double tot = 0;
@@ -1136,5 +1149,5 @@ int or_map(const or_grid *G, const or_state *S, const double obs[3], int nside_k
 
 /* Phase entry point for tests that drive the three steps one by one. */
 int or_run_phase(const or_grid *G, const or_params *P, or_state *S, int mode) {
-    return or_phase(G, P, S, mode);
+    return or_phase(G, P, S, mode, 0);
 }

@@ -120,6 +120,7 @@ def _bind(lib):
     lib.or_setup.argtypes = [P, P, P]
     lib.or_setup.restype = C.c_int64
     lib.or_direct.argtypes = [P, P, P]
+    lib.or_direct_incremental.argtypes = [P, P, P]
     lib.or_scatter_iter.argtypes = [P, P, P, P]
     lib.or_run_phase.argtypes = [P, P, P, C.c_int]
     lib.or_tau.argtypes = [P, C.c_int, P, P]
@@ -316,6 +317,16 @@ class Oracle:
     def direct(self):
         self._check(self._lib.or_direct(self._g.ref, C.byref(self._p), C.byref(self._s)))
 
+    def direct_incremental(self):
+        """Step 2 for a change of the emissivity, on top of the current U and
+        j_sca (dust self-heating iterations, Sect. 3.3)."""
+        self._check(self._lib.or_direct_incremental(self._g.ref, C.byref(self._p), C.byref(self._s)))
+
+    def set_emissivity(self, emis):
+        """Replace the per-leaf emissivity [n_leaf][n_lambda] (the C side
+        reads the float64 copy in place)."""
+        self._g.em[...] = np.asarray(emis, np.float64).reshape(self._g.em.shape)
+
     def run_phase(self, mode):
         self._check(self._lib.or_run_phase(self._g.ref, C.byref(self._p), C.byref(self._s), int(mode)))
 
@@ -364,3 +375,41 @@ class Oracle:
         self._check(self._lib.or_map(self._g.ref, C.byref(self._s), _ptr(obs), int(nside_k),
                                      int(max_sub), int(bool(use_jsca)), _ptr(out)))
         return out.reshape(g.n_lambda, -1)
+
+
+# --------------------------------------------------------------- dust emission
+def planck_lambda(lam_um, T):
+    """Synthetic Planck function per unit wavelength (lambda in um, T in K),
+    B = lambda^-5 / (exp(c2 / (lambda T)) - 1), c2 = hc/k = 14387.77 um K; the
+    physical prefactor 2hc^2 is absorbed in the dust model's scale."""
+    x = 14387.77 / (np.asarray(lam_um, np.float64) * np.asarray(T, np.float64))
+    with np.errstate(over="ignore"):  # exp(x) beyond the double range: B = 0
+        return np.asarray(lam_um, np.float64) ** -5 / np.expm1(x)
+
+
+def dust_emission(absorbed_power, kabs, volume, lam_um, dlam_um, scale, t_lo=2.0, t_hi=5000.0, iters=200):
+    """Equilibrium dust emission (Sect. 3.3, with a synthetic modified
+    blackbody in place of grain models): per cell, the temperature T where
+    the emitted power 4 pi V sum_i scale kabs_i B(lambda_i, T) dlambda_i
+    equals the absorbed power, by bisection in log T; returns T [n_cell] and
+    the emissivity j_i = scale kabs_i B(lambda_i, T) [n_cell][n_ir]
+    (luminosity per volume per sr per unit wavelength).  Cells that absorb
+    nothing, or have no dust, emit nothing."""
+    P = np.asarray(absorbed_power, np.float64)
+    k = np.asarray(kabs, np.float64)
+    V = np.asarray(volume, np.float64)
+
+    def emitted(T):
+        return 4 * np.pi * V * (scale * k * planck_lambda(lam_um[None, :], T[:, None]) * dlam_um[None, :]).sum(1)
+
+    lo = np.full(P.shape, np.log(t_lo))
+    hi = np.full(P.shape, np.log(t_hi))
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        low = emitted(np.exp(mid)) < P
+        lo = np.where(low, mid, lo)
+        hi = np.where(low, hi, mid)
+    T = np.exp(0.5 * (lo + hi))
+    active = (P > 0) & (k.sum(1) > 0)
+    j = np.where(active[:, None], scale * k * planck_lambda(lam_um[None, :], T[:, None]), 0.0)
+    return np.where(active, T, 0.0), j

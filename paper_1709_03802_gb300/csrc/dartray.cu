@@ -133,7 +133,8 @@ struct dartray_grid {
     int march_blocks = 1;
     int acc_blocks[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // resident blocks of cell_accumulate_kernel<1, 2, 6, 24> (x2: det)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    long long rec_cap = 0;
+    long long rec_cap = 0;    // record capacity in use (0: per-pixel atomic deposit); <= rec_alloc
+    long long rec_alloc = 0;  // record capacity allocated
     cudaEvent_t mev0 = nullptr, mev1 = nullptr;  // around each march launch (profile mode)
     double march_ms = 0.0, flush_ms = 0.0, busy_ms = 0.0, march_sum_ms = 0.0;
     long long march_launches = 0, restarts = 0, batches = 0;
@@ -168,6 +169,8 @@ struct dartray_grid {
     std::vector<double> m_lsca2, m_rem, m_fu;
     std::vector<unsigned char> m_active;
     std::vector<double> m_ledger;  // [n_models][LG_N][nl] of the last phase of the last call
+    float *d_jd = nullptr;         // dust emission of the last dartray_dust_emission call
+    unsigned *d_maxrel = nullptr;
     Exps eU{}, eJ{}, eL{};
     double *d_partial = nullptr, *h_partial = nullptr;  // deterministic sums
 };
@@ -181,7 +184,8 @@ void free_all(dartray_grid *g) {
                     g->d_src_pos, g->d_src_S, g->d_st, g->d_sum, g->d_stage, g->d_Ufix, g->d_pfix,
                     g->d_partial, g->d_mirror, g->d_mirror_pix, g->d_oct_u, g->d_oct_p, g->d_thr,
                     g->d_fu_model, g->d_models, g->d_leaf_model, g->d_point_model, g->d_model_active,
-                    g->d_mcount, g->d_mled, g->d_mled_fix, g->d_seg_beg, g->d_seg_len, g->d_seg_out};
+                    g->d_mcount, g->d_mled, g->d_mled_fix, g->d_seg_beg, g->d_seg_len, g->d_seg_out,
+                    g->d_jd, g->d_maxrel};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kPipes; ++i) {
@@ -571,7 +575,7 @@ int fix_exponent(double bound) {
 }
 
 // One phase (mode: step 1, step 2, one scattering iteration).
-int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
+int run_phase(dartray_grid *g, int mode, PhaseResult *res, bool keep_U = false) {
     cudaStream_t s = g->stream;
     const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
     if (mode == MODE_SCATTER) g->cur = 1 - g->cur;
@@ -686,6 +690,18 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
     double rays_per_src = rps_floor > 0.0 ? rps_floor
                                           : std::max(static_cast<double>(npix0) * 16.0, g->cap / 64.0);
     constexpr int kWavesAhead = 6;
+    // CUDA graphs of the pipelines' rounds of waves (not in the profile
+    // mode, which times every launch with events)
+    struct Graphs {
+        bool on = false;
+        cudaGraphExec_t exec[kPipes] = {nullptr, nullptr};
+        long long launches = 0;
+        ~Graphs() {
+            for (auto e : exec)
+                if (e) cudaGraphExecDestroy(e);
+        }
+    } graphs;
+    graphs.on = g->P.graphs != 0 && !g->P.profile;
     DevStats snap{};
     CK(cudaMemcpyAsync(&snap, g->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -694,7 +710,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
         if (mode == MODE_LL) {
             CK(cudaMemsetAsync(g->d_ULL, 0, nU * sizeof(float), s));
         } else {
-            if (mode == MODE_DIRECT) {
+            if (mode == MODE_DIRECT && !keep_U) {
                 CK(cudaMemsetAsync(g->d_U, 0, nU * sizeof(float), s));
             } else {
                 // U equals U_LL at the start of an iteration (U_LL <- U after each phase)
@@ -762,8 +778,37 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
                 }
                 if (P.active) {
                     any = true;
-                    for (int w = 0; w < kWavesAhead; ++w)
-                        if ((rc = enqueue_wave(g, P, i, mode, base, dep_pend, tm.get()))) return rc;
+                    if (graphs.on) {
+                        // the pipeline's kWavesAhead waves as one CUDA graph,
+                        // captured at its first use in the phase: every
+                        // kernel reads its work from the pipeline state in
+                        // device memory, so one graph serves every round
+                        if (!graphs.exec[i]) {
+                            const long long l0 = g->launches, m0 = g->march_launches;
+                            CK(cudaStreamBeginCapture(P.stream, cudaStreamCaptureModeThreadLocal));
+                            for (int w = 0; w < kWavesAhead && !rc; ++w)
+                                rc = enqueue_wave(g, P, i, mode, base, dep_pend, nullptr);
+                            cudaGraph_t gr = nullptr;
+                            const cudaError_t ce = cudaStreamEndCapture(P.stream, &gr);
+                            if (rc) {
+                                if (gr) cudaGraphDestroy(gr);
+                                return rc;
+                            }
+                            if (ce != cudaSuccess) return fail(DARTRAY_E_CUDA, cudaGetErrorString(ce));
+                            const cudaError_t ie = cudaGraphInstantiate(&graphs.exec[i], gr, 0);
+                            cudaGraphDestroy(gr);
+                            if (ie != cudaSuccess) return fail(DARTRAY_E_CUDA, cudaGetErrorString(ie));
+                            graphs.launches = g->launches - l0;
+                            g->launches = l0;
+                            g->march_launches = m0;
+                        }
+                        CK(cudaGraphLaunch(graphs.exec[i], P.stream));
+                        g->launches += graphs.launches;
+                        g->march_launches += kWavesAhead;
+                    } else {
+                        for (int w = 0; w < kWavesAhead; ++w)
+                            if ((rc = enqueue_wave(g, P, i, mode, base, dep_pend, tm.get()))) return rc;
+                    }
                     CK(cudaMemcpyAsync(P.h_pd, P.d_pd, sizeof(PipeDev), cudaMemcpyDeviceToHost, P.stream));
                     CK(cudaEventRecord(P.ev, P.stream));
                     inflight[i] = true;
@@ -875,7 +920,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
         // fixed point -> float: U (step 2 from zero, an iteration on top of
         // U_LL), U_LL in step 1, the pending j_sca rows
         const unsigned ub = static_cast<unsigned>((nU + kBlock - 1) / kBlock);
-        fix_to_u_kernel<<<ub, kBlock, 0, s>>>(g->G, g->d_Ufix, mode == MODE_SCATTER ? g->d_ULL : nullptr, g->eU,
+        fix_to_u_kernel<<<ub, kBlock, 0, s>>>(g->G, g->d_Ufix, mode == MODE_SCATTER || keep_U ? g->d_ULL : nullptr, g->eU,
                                               mode == MODE_LL ? g->d_ULL : g->d_U);
         ++g->launches;
         if (mode != MODE_LL) {
@@ -888,7 +933,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res) {
     }
     if (fold) {
         const unsigned ub = static_cast<unsigned>((nU + kBlock - 1) / kBlock);
-        octant_fold_u_kernel<<<ub, kBlock, 0, s>>>(g->G, g->d_oct_u, mode == MODE_SCATTER ? g->d_ULL : nullptr,
+        octant_fold_u_kernel<<<ub, kBlock, 0, s>>>(g->G, g->d_oct_u, mode == MODE_SCATTER || keep_U ? g->d_ULL : nullptr,
                                                    mode == MODE_LL ? g->d_ULL : g->d_U);
         ++g->launches;
         if (mode != MODE_LL) {
@@ -1006,6 +1051,7 @@ int dartray_params_default(dartray_params *p) {
     p->deposit_records = 0;
     p->deterministic = 0;
     p->octant = 0;
+    p->graphs = 1;
     return DARTRAY_OK;
 }
 
@@ -1057,7 +1103,7 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
         P.src_offset >= P.src_stride || P.max_cross < 1 || P.max_waves < 1 ||
         (P.queue_rays != 0 && P.queue_rays < 1024) || P.deposit_records < 0 ||
         !(P.c_light > 0) || P.a_rt < 0 || P.deterministic < 0 || P.deterministic > 1 || P.octant < 0 ||
-        P.octant > 1 || (P.octant && P.src_stride != 1))
+        P.octant > 1 || (P.octant && P.src_stride != 1) || P.graphs < 0 || P.graphs > 1)
         return fail(DARTRAY_E_INVAL, "invalid parameters");
     if (P.octant && n_models > 1) return fail(DARTRAY_E_INVAL, "the octant mode takes a single model");
     if (n_models > 1 && static_cast<long long>(n_models) * LG_N * nl * 8 > 32768)
@@ -1107,6 +1153,17 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
         err = build_topology(d.nroot, d.root_lo, d.root_size, d.n_nodes, d.n_leaf, fc.data(), lon.data(), &t);
         if (!err.empty()) return bail(fail(DARTRAY_E_INVAL, n_models > 1 ? "model " + std::to_string(m) + ": " + err : err));
         append_topology(&g->topo, t, static_cast<int>(node_off), static_cast<int>(leaf_off));
+        if (d.n_point > 0) {
+            // point sources must lie inside their model's root lattice
+            std::vector<float> pxyz;
+            if ((rc = fetch_host(pxyz, d.point_xyz, 3ull * d.n_point, dev_m))) return bail(rc);
+            for (int i = 0; i < d.n_point; ++i)
+                for (int a = 0; a < 3; ++a) {
+                    const double x = pxyz[3 * i + a];
+                    if (!(x >= d.root_lo[a] && x < d.root_lo[a] + d.nroot[a] * d.root_size))
+                        return bail(fail(DARTRAY_E_INVAL, "point source outside the model"));
+                }
+        }
         ModelDev &M = models[m];
         for (int a = 0; a < 3; ++a) {
             M.nroot[a] = d.nroot[a];
@@ -1176,9 +1233,10 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
     // grids, small for small grids
     g->cap = P.queue_rays > 0 ? P.queue_rays
                               : std::min<long long>(1ll << 27, std::max<long long>(1ll << 20, 512ll * tot_leaf));
-    g->rec_cap = P.deposit_direct ? 0
+    g->rec_alloc = P.deposit_direct ? 0
                  : (P.deposit_records > 0 ? P.deposit_records
                                           : std::min<long long>(1ll << 28, std::max<long long>(1ll << 20, 1024ll * tot_leaf)));
+    g->rec_cap = g->rec_alloc;
     // merge table: low lists are far smaller than waves; a wave whose low list
     // does not fit is retried with a smaller source batch
     g->hcap = 1;
@@ -1251,13 +1309,13 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
         AL(P.d_hmem, g->hcap);
         AL(P.d_pd, 1);
         AL(P.d_st, 1);
-        if (g->rec_cap > 0) {
-            AL(P.d_rec_cell, g->rec_cap);
-            AL(P.d_rec_dir, g->rec_cap);
-            AL(P.d_srt_dir, g->rec_cap);
+        if (g->rec_alloc > 0) {
+            AL(P.d_rec_cell, g->rec_alloc);
+            AL(P.d_rec_dir, g->rec_alloc);
+            AL(P.d_srt_dir, g->rec_alloc);
             if (nl > 1) {  // one wavelength: the coefficient is stored in the direction's w
-                AL(P.d_rec_coef, static_cast<size_t>(g->rec_cap) * nl);
-                AL(P.d_srt_coef, static_cast<size_t>(g->rec_cap) * nl);
+                AL(P.d_rec_coef, static_cast<size_t>(g->rec_alloc) * nl);
+                AL(P.d_srt_coef, static_cast<size_t>(g->rec_alloc) * nl);
             }
             AL(P.d_cnt, tot_leaf);
             AL(P.d_off, tot_leaf);
@@ -1500,6 +1558,155 @@ int dartray_scatter_iter(dartray_grid *g, double *remaining_frac, dartray_stats 
         stats->march_sum_ms = g->march_sum_ms;
         stats->batches = g->batches;
     }
+    return DARTRAY_OK;
+}
+
+int dartray_set_emissivity(dartray_grid *g, const float *emis, int src_is_device) {
+    g_last_error.clear();
+    if (!g || !emis) return fail(DARTRAY_E_INVAL, "null argument");
+    int rc = set_device(g);
+    if (rc) return rc;
+    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
+    if ((rc = copy_in(g->d_emis, emis, nU, src_is_device != 0, g->stream))) return rc;
+    CK(cudaStreamSynchronize(g->stream));
+    return DARTRAY_OK;
+}
+
+int dartray_direct_incremental(dartray_grid *g, dartray_stats *stats) {
+    g_last_error.clear();
+    if (!g) return fail(DARTRAY_E_INVAL, "null grid");
+    if (!g->have_direct) return fail(DARTRAY_E_STATE, "dartray_direct must run first");
+    int rc = set_device(g);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(g->d_st, 0, sizeof(DevStats), g->stream));
+    g->cur = 0;
+    const long long l0 = g->launches;
+    g->march_ms = g->flush_ms = g->busy_ms = g->march_sum_ms = 0.0;
+    g->march_launches = g->restarts = g->batches = 0;
+    std::fill(g->m_active.begin(), g->m_active.end(), 1);
+    CK(cudaMemcpyAsync(g->d_model_active, g->m_active.data(), g->n_models, cudaMemcpyHostToDevice, g->stream));
+    CK(cudaEventRecord(g->ev0, g->stream));
+    PhaseResult r{};
+    if ((rc = run_phase(g, MODE_DIRECT, &r, true))) return rc;
+    CK(cudaEventRecord(g->ev1, g->stream));
+    CK(cudaEventSynchronize(g->ev1));
+    g->l_sca2 = r.pend_sum;
+    if (stats) {
+        fill_stats(g, r, stats);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+        stats->gpu_ms = ms;
+        stats->kernel_launches = g->launches - l0;
+    }
+    return DARTRAY_OK;
+}
+
+int dartray_dust_emission(dartray_grid *ir, const dartray_grid *stellar, const dartray_dust *dust, float *T,
+                          float *j, int dst_is_device, double *max_rel_change) {
+    g_last_error.clear();
+    if (!ir || !stellar || !dust) return fail(DARTRAY_E_INVAL, "null argument");
+    if (ir->n_leaf != stellar->n_leaf || dust->n_ir != ir->nl || dust->n_stellar != stellar->nl ||
+        !(dust->scale > 0) || !(dust->t_min > 0) || !(dust->t_max > dust->t_min) || ir->device != stellar->device)
+        return fail(DARTRAY_E_INVAL, "dust emission: grids or parameters do not match");
+    int rc = set_device(ir);
+    if (rc) return rc;
+    cudaStream_t s = ir->stream;
+    const size_t nU = static_cast<size_t>(ir->n_leaf) * ir->nl;
+    if (!ir->d_jd) {
+        CK(cudaMalloc(reinterpret_cast<void **>(&ir->d_jd), nU * sizeof(float)));
+        CK(cudaMalloc(reinterpret_cast<void **>(&ir->d_maxrel), sizeof(unsigned)));
+        CK(cudaMemsetAsync(ir->d_jd, 0, nU * sizeof(float), s));
+    }
+    float *Tdev = nullptr;
+    if (T && !dst_is_device && (rc = stage_buffer(ir, ir->n_leaf, &Tdev))) return rc;
+    if (T && dst_is_device) Tdev = T;
+    // the stellar grid's work must be complete before its U is read
+    if (stellar->stream != s) CK(cudaStreamSynchronize(stellar->stream));
+    DustArgs D{};
+    D.n_leaf = ir->n_leaf;
+    D.n_ir = ir->nl;
+    D.n_st = stellar->nl;
+    for (int i = 0; i < ir->nl; ++i) {
+        D.lam[i] = dust->lam_ir[i];
+        D.dlam[i] = dust->dlam_ir[i];
+        D.alb_ir[i] = ir->G.albedo[i];
+    }
+    for (int i = 0; i < stellar->nl; ++i) {
+        D.dlam_st[i] = dust->dlam_stellar[i];
+        D.alb_st[i] = stellar->G.albedo[i];
+    }
+    D.scale = dust->scale;
+    D.t_lo = dust->t_min;
+    D.t_hi = dust->t_max;
+    D.c_light = ir->P.c_light;
+    D.U_ir = ir->d_U;
+    D.kr_ir = ir->d_kr;
+    D.U_st = stellar->d_U;
+    D.kr_st = stellar->d_kr;
+    D.leaf_box = ir->d_leaf_box;
+    D.j_prev = ir->d_jd;
+    D.emis = ir->d_emis;
+    D.T = Tdev;
+    D.max_rel = ir->d_maxrel;
+    CK(cudaMemsetAsync(ir->d_maxrel, 0, sizeof(unsigned), s));
+    dust_emission_kernel<<<(ir->n_leaf + kBlock - 1) / kBlock, kBlock, 0, s>>>(D);
+    ++ir->launches;
+    CK(cudaGetLastError());
+    unsigned bits = 0;
+    CK(cudaMemcpyAsync(&bits, ir->d_maxrel, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (j) CK(cudaMemcpyAsync(j, ir->d_jd, nU * sizeof(float), k, s));
+    if (T && !dst_is_device) CK(cudaMemcpyAsync(T, Tdev, ir->n_leaf * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float rel;
+    std::memcpy(&rel, &bits, sizeof rel);
+    if (max_rel_change) *max_rel_change = rel;
+    return DARTRAY_OK;
+}
+
+int dartray_autotune(dartray_grid *g, int32_t sample_stride, int32_t *choice, double *ms) {
+    g_last_error.clear();
+    if (!g || sample_stride < 1) return fail(DARTRAY_E_INVAL, "bad argument");
+    int rc = set_device(g);
+    if (rc) return rc;
+    // candidate deposit schedules: deferred records with the full buffer,
+    // deferred with a sixteenth of it (smaller, more frequent flushes), and
+    // per-pixel atomics in the marcher
+    const long long cand[3] = {g->rec_alloc, g->rec_alloc > 0 ? std::max<long long>(1ll << 20, g->rec_alloc / 16) : 0,
+                               0};
+    const int first = g->rec_alloc > 0 ? 0 : 2;
+    const int32_t stride0 = g->P.src_stride, offset0 = g->P.src_offset;
+    const double rps0[3] = {g->rays_per_src[0], g->rays_per_src[1], g->rays_per_src[2]};
+    g->P.src_stride = sample_stride;
+    g->P.src_offset = 0;
+    double best = 1e300;
+    int best_i = 2;
+    for (int i = 0; i < 3; ++i) {
+        if (ms) ms[i] = -1.0;
+        if (i < first) continue;
+        g->rec_cap = cand[i];
+        CK(cudaMemsetAsync(g->d_jtot, 0, g->sca_len * sizeof(float), g->stream));
+        g->cur = 0;
+        CK(cudaEventRecord(g->ev0, g->stream));
+        PhaseResult r1{}, r2{};
+        if ((rc = run_phase(g, MODE_LL, &r1)) || (rc = run_phase(g, MODE_DIRECT, &r2))) break;
+        CK(cudaEventRecord(g->ev1, g->stream));
+        CK(cudaEventSynchronize(g->ev1));
+        float t = 0.f;
+        cudaEventElapsedTime(&t, g->ev0, g->ev1);
+        if (ms) ms[i] = t;
+        if (t < best) {
+            best = t;
+            best_i = i;
+        }
+    }
+    g->P.src_stride = stride0;
+    g->P.src_offset = offset0;
+    for (int k = 0; k < 3; ++k) g->rays_per_src[k] = rps0[k];
+    g->rec_cap = cand[best_i];
+    g->have_direct = false;  // the trial phases leave no usable state
+    if (rc) return rc;
+    if (choice) *choice = best_i;
     return DARTRAY_OK;
 }
 

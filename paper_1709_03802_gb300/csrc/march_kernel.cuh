@@ -218,7 +218,9 @@ __global__ void __launch_bounds__(kMarchBlock, NL == 1 ? kMarchMinBlocks1 : (NL 
     // fixed-point add per event (per finished ray, seed or deposit run)
     auto ledger = [&](int slot, const float *v, float scale) {
         if (G.n_models > 1) {
-            unsigned long long *ml = sh_mled + (model_of_leaf(G, srcleaf) * LG_N + slot) * NL;
+            // the model of the ray's source (src is set for every ray,
+            // seeds included, before its first ledger entry)
+            unsigned long long *ml = sh_mled + (model_of_leaf(G, __ldg(&A.src_leaf[src])) * LG_N + slot) * NL;
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
                 const float x = v[l] * scale;

@@ -759,6 +759,72 @@ __global__ void octant_fold_jsca_kernel(const DevGrid G, int l, const float *dep
     }
 }
 
+// ------------------------------------------------------- dust emission
+// Equilibrium dust emission (Sect. 3.3) with a synthetic modified
+// blackbody in place of grain models.  Per cell: the absorbed power
+// P = sum over the stellar and the dust wavelengths of
+// (1 - albedo) kappa*rho c V U dlambda; the temperature T where
+// 4 pi V sum_i scale kabs_i B(lambda_i, T) dlambda_i = P (bisection in log T,
+// double); the emissivity j_i = scale kabs_i B(lambda_i, T), with
+// kabs_i = (1 - albedo_i) kappa*rho_i and B = lambda^-5 / (exp(c2 / (lambda T)) - 1)
+// (lambda in um, c2 = 14387.77 um K).  The grid's emissivity becomes the
+// change j - j_prev (clipped at 0), which the next self-heating step
+// processes; j_prev <- j.
+struct DustArgs {
+    int n_leaf, n_ir, n_st;
+    double lam[kMaxLambda], dlam[kMaxLambda], dlam_st[kMaxLambda];
+    double scale, t_lo, t_hi, c_light;
+    float alb_ir[kMaxLambda], alb_st[kMaxLambda];
+    const float *U_ir, *kr_ir, *U_st, *kr_st;
+    const float4 *leaf_box;
+    float *j_prev;      // [n_leaf][n_ir] dust emissivity of the previous call
+    float *emis;        // [n_leaf][n_ir] the grid's emissivity: the change to process
+    float *T;           // [n_leaf] or null
+    unsigned *max_rel;  // float bits of the largest relative change of j (non-negative)
+};
+
+__device__ inline double planck_um(double lam, double T) { return pow(lam, -5.0) / expm1(14387.77 / (lam * T)); }
+
+__global__ void dust_emission_kernel(const DustArgs D) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= D.n_leaf) return;
+    const double L = D.leaf_box[c].w, V = L * L * L;
+    double P = 0.0;
+    for (int s = 0; s < D.n_st; ++s)
+        P += (1.0 - D.alb_st[s]) * D.kr_st[static_cast<long long>(c) * D.n_st + s] * D.c_light * V *
+             D.U_st[static_cast<long long>(c) * D.n_st + s] * D.dlam_st[s];
+    double kabs[kMaxLambda], ksum = 0.0;
+    for (int i = 0; i < D.n_ir; ++i) {
+        kabs[i] = (1.0 - D.alb_ir[i]) * D.kr_ir[static_cast<long long>(c) * D.n_ir + i];
+        ksum += kabs[i];
+        P += kabs[i] * D.c_light * V * D.U_ir[static_cast<long long>(c) * D.n_ir + i] * D.dlam[i];
+    }
+    double T = 0.0;
+    if (P > 0.0 && ksum > 0.0) {
+        double lo = log(D.t_lo), hi = log(D.t_hi);
+        for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi), Tm = exp(mid);
+            double e = 0.0;
+            for (int i = 0; i < D.n_ir; ++i) e += D.scale * kabs[i] * planck_um(D.lam[i], Tm) * D.dlam[i];
+            if (4.0 * kPi * V * e < P) lo = mid;
+            else hi = mid;
+        }
+        T = exp(0.5 * (lo + hi));
+    }
+    float rel = 0.f;
+    for (int i = 0; i < D.n_ir; ++i) {
+        const long long k = static_cast<long long>(c) * D.n_ir + i;
+        const float j = T > 0.0 ? static_cast<float>(D.scale * kabs[i] * planck_um(D.lam[i], T)) : 0.f;
+        const float jp = D.j_prev[k];
+        D.emis[k] = fmaxf(j - jp, 0.f);
+        if (jp > 0.f) rel = fmaxf(rel, fabsf(j - jp) / jp);
+        else if (j > 0.f) rel = __int_as_float(0x7f800000);
+        D.j_prev[k] = j;
+    }
+    if (D.T) D.T[c] = static_cast<float>(T);
+    if (rel > 0.f) atomicMax(D.max_rel, __float_as_uint(rel));  // non-negative floats order as their bits
+}
+
 // Deterministic sum of n floats: a fixed grid, each block's partial (double)
 // summed in a fixed order; the host adds the partials in order.
 constexpr int kSumBlocks = 1024;

@@ -42,7 +42,8 @@ class dartray_params(C.Structure):
                 ("merge", C.c_int32), ("max_cross", C.c_int32), ("max_waves", C.c_int32),
                 ("src_stride", C.c_int32), ("src_offset", C.c_int32), ("queue_rays", C.c_int64),
                 ("src_batch", C.c_int64), ("profile", C.c_int32), ("deposit_direct", C.c_int32),
-                ("deposit_records", C.c_int64), ("deterministic", C.c_int32), ("octant", C.c_int32)]
+                ("deposit_records", C.c_int64), ("deterministic", C.c_int32), ("octant", C.c_int32),
+                ("graphs", C.c_int32)]
 
 
 _L = MAX_LAMBDA
@@ -100,6 +101,7 @@ def load(build_if_missing=True):
         "dartray_grid_create_batch": ([P, C.c_int32, P, P, P], C.c_int),
         "dartray_model_info": ([P, C.c_int32, P, P, P, P, P], C.c_int),
         "dartray_model_stats": ([P, C.c_int32, P], C.c_int),
+        "dartray_autotune": ([P, C.c_int32, P, P], C.c_int),
         "dartray_state_load": ([P, C.c_char_p], C.c_int),
         "dartray_grid_destroy": ([P], None),
         "dartray_last_error": ([], C.c_char_p),
@@ -115,7 +117,7 @@ def load(build_if_missing=True):
 EXPORTED = ("dartray_params_default", "dartray_grid_create", "dartray_direct", "dartray_scatter_iter",
             "dartray_rfed", "dartray_jsca_layout", "dartray_jsca", "dartray_map", "dartray_map_noalloc",
             "dartray_state_save", "dartray_state_load", "dartray_grid_destroy", "dartray_last_error",
-            "dartray_grid_create_batch", "dartray_model_info", "dartray_model_stats")
+            "dartray_grid_create_batch", "dartray_model_info", "dartray_model_stats", "dartray_autotune")
 
 
 def _check(rc):
@@ -307,6 +309,14 @@ class DartRay:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, sample_stride=64):
+        """Pick the fastest deposit schedule (dartray_autotune); returns its
+        index and the trial times in ms."""
+        choice = C.c_int32()
+        ms = (C.c_double * 3)()
+        _check(load().dartray_autotune(self._h, int(sample_stride), C.byref(choice), ms))
+        return choice.value, list(ms)
 
     def direct(self):
         self.last_stats = dartray_direct(self._h).to_dict(self.n_lambda)
