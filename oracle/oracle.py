@@ -413,3 +413,173 @@ def dust_emission(absorbed_power, kabs, volume, lam_um, dlam_um, scale, t_lo=2.0
     active = (P > 0) & (k.sum(1) > 0)
     j = np.where(active[:, None], scale * k * planck_lambda(lam_um[None, :], T[:, None]), 0.0)
     return np.where(active, T, 0.0), j
+
+
+def absorbed_power(oracles, dlams):
+    """Per-cell absorbed power summed over the wavelengths of one or more
+    oracle runs on the same grid: sum of (1 - albedo) kappa*rho c V U dlambda
+    (Sect. 3.3: the dust is heated by everything it absorbs)."""
+    P = 0.0
+    for o, dl in zip(oracles, dlams):
+        U, L_abs = o.rfed()
+        P = P + (L_abs * np.asarray(dl, np.float64)[None, :]).sum(1)
+    return P
+
+
+def dust_self_heating(stellar, dust, lam_ir, dlam_ir, dlam_stellar, scale, f_l=0.01, tol=0.01, max_steps=20,
+                      max_iters=12):
+    """The self-heating procedure of Sect. 3.3 on two oracles of one grid
+    (stellar wavelengths, dust wavelengths), in the paper's order:
+    1. dust emission from the absorbed stellar light;
+    2. the dust emission RT (steps 1-3 of Sect. 2);
+    3. the emission recomputed from the absorbed stellar and dust light;
+    4. its change;
+    5. an RT of the change only (no U_LL step; U and j_sca continue);
+    6. 3-5 until the change is below tol everywhere.
+    Returns T, j and the per-step history."""
+    g = dust.grid
+    V = g.leaf_size.astype(np.float64) ** 3
+    kabs = (1.0 - g.albedo.astype(np.float64))[None, :] * g.kappa_rho.astype(np.float64)
+    lam = np.asarray(lam_ir, np.float64)
+    dl = np.asarray(dlam_ir, np.float64)
+    T, j = dust_emission(absorbed_power([stellar], [dlam_stellar]), kabs, V, lam, dl, scale)
+    dust.set_emissivity(j)
+    j_prev = j
+    dust.direct()
+    hist = []
+    for step in range(max_steps):
+        cross = dust.stats()[1]["crossings"]
+        for _ in range(max_iters):
+            rem = dust.scatter_iter()
+            cross += dust.stats()[1]["crossings"]
+            if rem < f_l:
+                break
+        T, j = dust_emission(absorbed_power([stellar, dust], [dlam_stellar, dl]), kabs, V, lam, dl, scale)
+        change = j - j_prev
+        with np.errstate(divide="ignore", invalid="ignore"):
+            rel = np.where(j_prev > 0, np.abs(change) / j_prev, np.where(j > 0, np.inf, 0.0))
+        rel = float(rel.max()) if rel.size else 0.0
+        hist.append(dict(step=step, max_rel_change=rel, crossings=cross))
+        dust.set_emissivity(np.maximum(change, 0.0))
+        j_prev = j
+        if rel < tol:
+            break
+        dust.direct_incremental()
+    return T, j, hist
+
+
+# --------------------------------------------------------------- external maps
+def external_frame(view, up):
+    """Unit view direction w (model -> observer), image up u (orthogonal to
+    w) and right r = u x w."""
+    w = np.asarray(view, np.float64) / np.linalg.norm(view)
+    u = np.asarray(up, np.float64) - np.dot(up, w) * w
+    u /= np.linalg.norm(u)
+    return w, u, np.cross(u, w)
+
+
+def _cell_emission(eta, kr, ds):
+    """E = eta (1 - e^{-kr ds}) / kr (eta ds for kr = 0) and dE/dkr."""
+    x = kr * ds
+    with np.errstate(divide="ignore", invalid="ignore"):
+        omT = -np.expm1(-x)
+        E = np.where(x > 0, eta * omT / np.where(kr > 0, kr, 1.0), eta * ds)
+        dE = np.where(x > 1e-8, eta * (ds * (1 - omT) * kr - omT) / np.where(kr > 0, kr * kr, 1.0),
+                      -0.5 * eta * ds * ds)
+    return E, dE
+
+
+class ExternalMapOracle:
+    """Orthographic map for a distant observer (Sect. 2, end: I_obs = I_0
+    e^-tau along each line of sight, the cells as a continuous medium) and its
+    vector-Jacobian product with respect to kappa*rho, the source held fixed;
+    plain line-by-line evaluation in double."""
+
+    def __init__(self, oracle, view, up, origin, pixel, nx, ny, use_jsca=True):
+        self.o, self.g = oracle, oracle.grid
+        self.w, self.u, self.r = external_frame(view, up)
+        self.origin, self.px, self.nx, self.ny = np.asarray(origin, np.float64), float(pixel), int(nx), int(ny)
+        g = self.g
+        self.lo = np.asarray(g.root_lo, np.float64)
+        self.hi = self.lo + np.asarray(g.nroot, np.float64) * g.root_size
+        # source toward the observer: emissivity plus the total scattered
+        # luminosity of the j_sca pixel holding w, per its solid angle, per volume
+        V = g.leaf_size.astype(np.float64) ** 3
+        self.eta_sca = np.zeros((g.n_leaf, g.n_lambda))
+        if use_jsca:
+            for l in range(g.n_lambda):
+                k = oracle.k_lam[l]
+                q = vec2pix(k, self.w)
+                self.eta_sca[:, l] = oracle.jsca(l, "total")[:, q] / (4 * np.pi / (12 * 4 ** k)) / V
+        self.eta = g.emissivity.astype(np.float64) + self.eta_sca
+        self.h = _GridHandle(g)
+
+    def segments(self, i, j):
+        """Leaves and chords along pixel (i, j)'s line of sight, front to back."""
+        p0 = (self.origin[0] + (i + 0.5) * self.px) * self.r + (self.origin[1] + (j + 0.5) * self.px) * self.u
+        d = -self.w
+        with np.errstate(divide="ignore"):
+            ta, tb = (self.lo - p0) / d, (self.hi - p0) / d
+        t0 = np.max(np.where(d != 0, np.minimum(ta, tb), -np.inf))
+        t1 = np.min(np.where(d != 0, np.maximum(ta, tb), np.inf))
+        inside = np.all((d != 0) | ((p0 >= self.lo) & (p0 < self.hi)))
+        if not (t1 > t0) or not inside:
+            return np.zeros(0, np.int64), np.zeros(0)
+        xs = np.clip(p0 + t0 * d, self.lo, self.hi)
+        leaf, tin, tout = trace(self.h, xs, d)
+        return leaf.astype(np.int64), tout - tin
+
+    def kappa(self):
+        return self.g.kappa_rho.astype(np.float64)
+
+    def pixel(self, i, j, kr=None):
+        kr = self.kappa() if kr is None else kr
+        leaf, ds = self.segments(i, j)
+        out = np.zeros(self.g.n_lambda)
+        for l in range(self.g.n_lambda):
+            E, _ = _cell_emission(self.eta[leaf, l], kr[leaf, l], ds)
+            T = np.exp(-kr[leaf, l] * ds)
+            Tf = np.concatenate([[1.0], np.cumprod(T)[:-1]])
+            out[l] = (E * Tf).sum()
+        return out
+
+    def map(self, kr=None, eta=None):
+        m = np.zeros((self.g.n_lambda, self.ny, self.nx))
+        saved = self.eta
+        if eta is not None:
+            self.eta = eta
+        try:
+            for j in range(self.ny):
+                for i in range(self.nx):
+                    m[:, j, i] = self.pixel(i, j, kr)
+        finally:
+            self.eta = saved
+        return m
+
+    def vjp_albedo(self, dmap, kr=None):
+        """d/d albedo_l of sum(dmap * map), the radiation field held fixed:
+        j_sca is the albedo times a field-only quantity, so the derivative is
+        the map of the scattered light alone divided by the albedo."""
+        ms = self.map(kr, eta=self.eta_sca)
+        a = self.g.albedo.astype(np.float64)
+        return np.where(a > 0, (dmap * ms).sum(axis=(1, 2)) / np.where(a > 0, a, 1.0), 0.0)
+
+    def vjp(self, dmap, kr=None):
+        """grad[c][l] = sum over pixels of dmap d map / d kappa_rho[c][l]:
+        d SB / d kr_c = T_front dE_c/dkr - ds_c (sum of the contributions of
+        the cells behind c)."""
+        kr = self.kappa() if kr is None else kr
+        grad = np.zeros_like(kr)
+        for j in range(self.ny):
+            for i in range(self.nx):
+                leaf, ds = self.segments(i, j)
+                if leaf.size == 0:
+                    continue
+                for l in range(self.g.n_lambda):
+                    E, dE = _cell_emission(self.eta[leaf, l], kr[leaf, l], ds)
+                    T = np.exp(-kr[leaf, l] * ds)
+                    Tf = np.concatenate([[1.0], np.cumprod(T)[:-1]])
+                    contrib = E * Tf
+                    behind = np.concatenate([np.cumsum(contrib[::-1])[::-1][1:], [0.0]])
+                    np.add.at(grad[:, l], leaf, dmap[l, j, i] * (Tf * dE - ds * behind))
+        return grad
