@@ -255,27 +255,75 @@ def bench_batched(params):
 
     def sweep8():
         s1 = one.direct()
+        U_direct = one.rfed()[0].copy()
         _, s2 = one.scatter_iter()
-        return s1["crossings"] + s2["crossings"]
+        return s1["crossings"] + s2["crossings"], U_direct
 
-    c8, t8 = timed_call(sweep8)
+    (c8, U8d), t8 = timed_call(sweep8)
     U8 = one.rfed()[0].copy()
     one.close()
-    t1, worst = 0.0, 0.0
+    t1, c1, worst, worst_d = 0.0, 0, 0.0, 0.0
     for l in range(8):
         gl = g8.with_lambda(g8.kappa_rho[:, l:l + 1], g8.emissivity[:, l:l + 1], g8.albedo[l:l + 1], g8.g[l:l + 1])
         gg = DartRay(gl, **p, **cap)
-        _, dt = timed_call(lambda: (gg.direct(), gg.scatter_iter()))
+
+        def sweep1():
+            s1 = gg.direct()
+            U_direct = gg.rfed()[0][:, 0].copy()
+            _, s2 = gg.scatter_iter()
+            return s1["crossings"] + s2["crossings"], U_direct
+
+        (c, U1d), dt = timed_call(sweep1)
         t1 += dt
+        c1 += c
         U1 = gg.rfed()[0][:, 0]
         big = U1 > 1e-6 * U1.max()
         worst = max(worst, float(np.abs(U8[big, l] / U1[big] - 1).max()))
+        big = U1d > 1e-6 * U1d.max()
+        worst_d = max(worst_d, float(np.abs(U8d[big, l] / U1d[big] - 1).max()))
         gg.close()
     out["wavelengths"] = {"workload": "galaxy at 8 wavelengths 0.15-2.2 um, every 64th source, steps 1-2 + one "
                                       "scattering iteration",
                           "plain_loop_s": t1, "batched_s": t8, "speedup": t1 / t8, "crossings": int(c8),
-                          "max_rel_diff_U": worst}
+                          "plain_crossings": int(c1),
+                          "max_rel_diff_U_after_step2": worst_d, "max_rel_diff_U": worst,
+                          "note": "scattering rays of a multi-wavelength grid start at the finest j_sca level of "
+                                  "its wavelengths, so the scattered part differs by that angular sampling"}
     return out
+
+
+def bench_clumpy(peak):
+    """Crossings/s on a clumpy grid beside the galaxy: the 64^3 lognormal cube
+    (sigma_ln rho = 1, mean edge-to-edge tau_V = 2, 16 emitting cells drawn
+    with probability proportional to the density), steps 1-2 and scattering
+    iterations to f_L, every launch timed by CUDA events on its stream."""
+    import synth
+    from paper_1709_03802_gb300 import DartRay
+    grid = synth.lognormal_cube(64, 4, tau_mean=2.0, n_src=16)
+    g = DartRay(grid, profile=1, **dict(PARAMS, r_pre=0.15 * 2.0))
+    tot = {"crossings": 0, "records": 0, "march_sum_ms": 0.0, "gpu_ms": 0.0}
+    it_ms = []
+
+    def add(st):
+        for k in tot:
+            tot[k] += st[k]
+
+    add(g.direct())
+    for _ in range(MAX_ITERS):
+        rem, st = g.scatter_iter()
+        add(st)
+        it_ms.append(st["gpu_ms"])
+        if rem < F_L:
+            break
+    g.close()
+    alg = tot["crossings"] * bytes_per_crossing(1) + RECORD_BYTES * tot["records"]
+    ach = alg / (tot["march_sum_ms"] / 1e3) / 1e9 if tot["march_sum_ms"] > 0 else None
+    return {"workload": "64^3 lognormal cube (sigma_ln rho 1, mean tau_V 2, 16 emitting cells), steps 1-2 + "
+                        f"scattering iterations to f_L = {F_L}",
+            "n_leaf": grid.n_leaf, "value": tot["crossings"] / (tot["gpu_ms"] / 1e3), "unit": "crossings/s",
+            "crossings": int(tot["crossings"]), "seconds": tot["gpu_ms"] / 1e3,
+            "s_per_scatter_iter": float(np.mean(it_ms)) / 1e3, "scatter_iters": len(it_ms),
+            "march_kernel_achieved_gbs": ach, "march_kernel_frac": ach / peak if ach else None}
 
 
 def cpu_sample(grid, params, stride, offset=0):
@@ -355,7 +403,8 @@ def main():
     unit = "crossings/s"
     config = {"workload": WORKLOAD, "n_leaf": grid.n_leaf, "a_rt": params["a_rt"], "f_l": F_L,
               "map": f"nside 64 at {OBSERVER} kpc", "l2": "flushed between steps (512 MB write)",
-              "warmup_note": "the first warm-up step is the end-to-end run through host buffers"}
+              "warmup_note": "warm-up 1 is the end-to-end run through host buffers, warm-up 2 the profiled step "
+                              "the roofline figures come from"}
     if args.src_stride > 1:
         config["profiling_subset"] = f"every {args.src_stride}th primary source (not a bench value)"
     if args.queue_rays or args.deposit_records:
@@ -417,9 +466,26 @@ def main():
         g2.close()
         del g2
 
-    gpu = DartRay(grid, profile=1, **params)
+    # warm-up 2: one step with every ray-march launch and deposit flush timed
+    # by CUDA events on its pipeline stream (params.profile), for the
+    # roofline figures; the timed steps below run without those events, with
+    # each pipeline's rounds of waves replayed as CUDA graphs
+    prof = None
+    if args.warmup >= 2:
+        gp = DartRay(grid, profile=1, **params)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        prof = run_step(gp, grid)
+        e1.record()
+        torch.cuda.synchronize()
+        prof["step_ms"] = e0.elapsed_time(e1)
+        gp.close()
+        del gp
+
+    gpu = DartRay(grid, **params)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(max(0, args.warmup - 1)):
+    for _ in range(max(0, args.warmup - 2)):
         run_step(gpu, grid)
     torch.cuda.synchronize()
     results = []
@@ -444,31 +510,35 @@ def main():
     cross = float(np.mean([r["crossings"] for r in results]))
     value = whole_job_rate(cross, world, ms)
     it_ms = [x for r in results for x in r["iter_ms"]]
-    march_ms = sum(r["march_ms"] for r in results)
     nl = grid.n_lambda
-    # algorithmic bytes of the marcher: per crossing (leaf box, face link, node
-    # word, kappa*rho, U_LL, U read-modify-write) plus one 24-byte deposit
-    # record per depositing crossing (j_sca pixels / pixels per row)
-    alg_bytes = sum(r["march_crossings"] * bytes_per_crossing(nl) + RECORD_BYTES * r["records"] for r in results)
     peak, peak_src = peaks()
-    # per launch: algorithmic bytes / the launch's CUDA-event span on its
-    # stream, averaged over the launches (= all bytes / summed spans; a span
-    # includes any wait for SMs held by the other pipeline's kernels)
-    march_sum_ms = sum(r["march_sum_ms"] for r in results)
-    launches = sum(r["march_launches"] for r in results)
-    achieved = alg_bytes / (march_sum_ms / 1e3) / 1e9 if march_sum_ms > 0 else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "kernel": "march_kernel (ray marcher)", "peak_source": peak_src,
-                "launches": launches, "avg_launch_ms": march_sum_ms / launches if launches else None,
-                "achieved_over_busy_union": alg_bytes / (march_ms / 1e3) / 1e9 if march_ms > 0 else None,
-                "kernel_busy_share_of_step": march_ms / total_ms if total_ms else None,
-                "deposit_flush_share_of_step": (sum(r["flush_ms"] for r in results) / total_ms
-                                                if total_ms else None)}
+    roofline = None
+    if prof is not None:
+        # algorithmic bytes of the marcher in the profiled step: per crossing
+        # (leaf box, face link, node word, kappa*rho, U_LL, U read-modify-write)
+        # plus one deposit record per depositing crossing
+        alg_bytes = prof["march_crossings"] * bytes_per_crossing(nl) + RECORD_BYTES * prof["records"]
+        # per launch: algorithmic bytes / the launch's CUDA-event span on its
+        # stream, averaged over the launches (= all bytes / summed spans; a span
+        # includes any wait for SMs held by the other pipeline's kernels)
+        march_sum_ms, launches = prof["march_sum_ms"], prof["march_launches"]
+        achieved = alg_bytes / (march_sum_ms / 1e3) / 1e9 if march_sum_ms > 0 else None
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": (achieved / peak) if achieved else None, "traffic": None,
+                    "kernel": "march_kernel (ray marcher)", "peak_source": peak_src,
+                    "launches": launches, "avg_launch_ms": march_sum_ms / launches if launches else None,
+                    "bytes_per_crossing": bytes_per_crossing(nl), "record_bytes": RECORD_BYTES,
+                    "crossings_profiled_step": prof["march_crossings"], "records_profiled_step": prof["records"],
+                    "achieved_over_busy_union": alg_bytes / (prof["march_ms"] / 1e3) / 1e9
+                    if prof["march_ms"] > 0 else None,
+                    "kernel_busy_share_of_step": prof["march_ms"] / prof["step_ms"],
+                    "deposit_flush_share_of_step": prof["flush_ms"] / prof["step_ms"],
+                    "note": "from warm-up step 2, whose launches are timed with CUDA events"}
     gpu.close()
-    batched = None
+    batched = clumpy = None
     if not args.no_batched and args.src_stride == 1:
         batched = bench_batched(params)
+        clumpy = bench_clumpy(peak)
 
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.src_stride == 1:
@@ -487,7 +557,7 @@ def main():
                 "deposit_records_per_step": float(np.mean([r["records"] for r in results])),
                 "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
                 "gpu_launches": int(sum(r["launches"] for r in results)), "clocks": clocks,
-                "batched_vs_plain": batched}
+                "batched_vs_plain": batched, "clumpy_grid": clumpy}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

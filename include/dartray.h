@@ -269,6 +269,42 @@ typedef struct dartray_dust {
 int dartray_dust_emission(dartray_grid *dust_grid, const dartray_grid *stellar_grid, const dartray_dust *dust,
                           float *T, float *j, int dst_is_device, double *max_rel_change);
 
+/*
+ * Surface-brightness map for a distant observer (orthographic; Sect. 2, end:
+ * I_obs = I_0 e^-tau along each line of sight, the cells treated as a
+ * continuous medium).  view: unit vector from the model toward the
+ * observer; up: the image's up direction (made orthogonal to view); right =
+ * up x view.  Pixel (i, j) is the line of sight through
+ * origin[0] + (i + 1/2) pixel along right and origin[1] + (j + 1/2) pixel
+ * along up (image-plane coordinates through the coordinate origin), parallel
+ * to -view.  Front to back, a cell crossed over ds with extinction kr adds
+ * eta (1 - e^{-kr ds}) / kr (eta ds if kr = 0) times the transmission in
+ * front of it; eta = emissivity + j_sca_total[pixel of view] / (Omega V)
+ * (use_jsca = 0: the stellar emissivity alone).  map: [n_lambda][ny][nx],
+ * luminosity per area per sr, host or device.  Single-model grids.
+ * Errors: INVAL, CUDA.
+ */
+int dartray_map_external(dartray_grid *grid, const double view[3], const double up[3], const double origin[2],
+                         double pixel, int32_t nx, int32_t ny, int32_t use_jsca, float *map, int dst_is_device);
+
+/* Vector-Jacobian product of dartray_map_external, the radiation field of
+ * the last sweep held fixed: grad_kappa_rho[c][l] = sum over pixels of
+ * dmap[l][pixel] d map[l][pixel] / d kappa_rho[c][l] (the source eta held
+ * fixed), and grad_albedo[l] = the same for the albedo, through j_sca, which
+ * is proportional to it at a fixed radiation field (null: not wanted).  The
+ * transmission is recomputed along every line of sight (two passes) instead
+ * of stored.  dmap [n_lambda][ny][nx] and grad_kappa_rho [n_leaf][n_lambda]
+ * are both host or both device memory; grad_albedo [n_lambda] is host
+ * memory.  Errors: INVAL, CUDA. */
+int dartray_map_external_vjp(dartray_grid *grid, const double view[3], const double up[3], const double origin[2],
+                             double pixel, int32_t nx, int32_t ny, int32_t use_jsca, const float *dmap,
+                             float *grad_kappa_rho, double *grad_albedo, int on_device);
+
+/* Replace kappa_rho [n_leaf][n_lambda] (host or device), e.g. to map a
+ * changed dust distribution; the RFED and j_sca keep their values until the
+ * next sweep. */
+int dartray_set_kappa_rho(dartray_grid *grid, const float *kappa_rho, int src_is_device);
+
 /* Replace the emissivity [n_leaf][n_lambda] (host or device). */
 int dartray_set_emissivity(dartray_grid *grid, const float *emissivity, int src_is_device);
 

@@ -1561,6 +1561,115 @@ int dartray_scatter_iter(dartray_grid *g, double *remaining_frac, dartray_stats 
     return DARTRAY_OK;
 }
 
+namespace {
+
+// image-plane frame of an external map: right = up x view, up made
+// orthogonal to view
+int external_frame(dartray_grid *g, const double view[3], const double up[3], const double origin[2], double pixel,
+                   int32_t nx, int32_t ny, ExtMapArgs *M) {
+    if (g->n_models > 1) return fail(DARTRAY_E_INVAL, "maps are made of single-model grids");
+    if (nx < 1 || ny < 1 || static_cast<long long>(nx) * ny > (1ll << 26) || !(pixel > 0))
+        return fail(DARTRAY_E_INVAL, "bad image size");
+    double vn = std::sqrt(view[0] * view[0] + view[1] * view[1] + view[2] * view[2]);
+    if (!(vn > 0)) return fail(DARTRAY_E_INVAL, "bad view direction");
+    double w[3] = {view[0] / vn, view[1] / vn, view[2] / vn};
+    double u[3] = {up[0], up[1], up[2]};
+    const double uw = u[0] * w[0] + u[1] * w[1] + u[2] * w[2];
+    for (int a = 0; a < 3; ++a) u[a] -= uw * w[a];
+    const double un = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (!(un > 1e-12)) return fail(DARTRAY_E_INVAL, "up is parallel to view");
+    for (int a = 0; a < 3; ++a) u[a] /= un;
+    const double r[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+    for (int a = 0; a < 3; ++a) {
+        M->view[a] = w[a];
+        M->up[a] = u[a];
+        M->right[a] = r[a];
+        M->box_lo[a] = g->G.root_lo[a];
+        M->box_hi[a] = static_cast<double>(g->G.root_lo[a]) + static_cast<double>(g->G.nroot[a]) * g->G.root_size;
+    }
+    M->origin[0] = origin[0];
+    M->origin[1] = origin[1];
+    M->px = pixel;
+    M->nx = nx;
+    M->ny = ny;
+    return DARTRAY_OK;
+}
+
+}  // namespace
+
+int dartray_map_external(dartray_grid *g, const double view[3], const double up[3], const double origin[2],
+                         double pixel, int32_t nx, int32_t ny, int32_t use_jsca, float *map, int dst_is_device) {
+    g_last_error.clear();
+    if (!g || !view || !up || !origin || !map) return fail(DARTRAY_E_INVAL, "null argument");
+    ExtMapArgs M{};
+    int rc = external_frame(g, view, up, origin, pixel, nx, ny, &M);
+    if (rc) return rc;
+    if ((rc = set_device(g))) return rc;
+    const size_t n = static_cast<size_t>(nx) * ny * g->nl;
+    float *dst = map;
+    if (!dst_is_device && (rc = stage_buffer(g, n, &dst))) return rc;
+    M.jsca = use_jsca ? g->d_jtot : nullptr;
+    M.map = dst;
+    if (launch_external_map(g->G, M, false, g->stream)) return fail(DARTRAY_E_INVAL, "unsupported n_lambda");
+    ++g->launches;
+    CK(cudaGetLastError());
+    if (!dst_is_device) CK(cudaMemcpyAsync(map, dst, n * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return DARTRAY_OK;
+}
+
+int dartray_map_external_vjp(dartray_grid *g, const double view[3], const double up[3], const double origin[2],
+                             double pixel, int32_t nx, int32_t ny, int32_t use_jsca, const float *dmap,
+                             float *grad_kappa_rho, double *grad_albedo, int on_device) {
+    g_last_error.clear();
+    if (!g || !view || !up || !origin || !dmap || !grad_kappa_rho) return fail(DARTRAY_E_INVAL, "null argument");
+    ExtMapArgs M{};
+    int rc = external_frame(g, view, up, origin, pixel, nx, ny, &M);
+    if (rc) return rc;
+    if ((rc = set_device(g))) return rc;
+    const size_t n = static_cast<size_t>(nx) * ny * g->nl, nU = static_cast<size_t>(g->n_leaf) * g->nl;
+    // the grid's staging buffer holds the per-wavelength sums (doubles, at
+    // its start) and, for host arguments, the upstream gradient and the result
+    const size_t n_dbl = 2 * kMaxLambda;  // in floats
+    float *st = nullptr;
+    if ((rc = stage_buffer(g, n_dbl + (on_device ? 0 : n + nU), &st))) return rc;
+    double *d_gs = reinterpret_cast<double *>(st);
+    float *d_in = const_cast<float *>(dmap), *d_out = grad_kappa_rho;
+    if (!on_device) {
+        d_in = st + n_dbl;
+        d_out = st + n_dbl + n;
+        CK(cudaMemcpyAsync(d_in, dmap, n * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+    }
+    CK(cudaMemsetAsync(d_out, 0, nU * sizeof(float), g->stream));
+    CK(cudaMemsetAsync(d_gs, 0, kMaxLambda * sizeof(double), g->stream));
+    M.jsca = use_jsca ? g->d_jtot : nullptr;
+    M.dmap = d_in;
+    M.grad = d_out;
+    M.grad_sca = d_gs;
+    if (launch_external_map(g->G, M, true, g->stream)) return fail(DARTRAY_E_INVAL, "unsupported n_lambda");
+    ++g->launches;
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(grad_kappa_rho, d_out, nU * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    double gs[kMaxLambda];
+    CK(cudaMemcpyAsync(gs, d_gs, g->nl * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    // j_sca is proportional to the albedo (the radiation field held fixed)
+    if (grad_albedo)
+        for (int l = 0; l < g->nl; ++l) grad_albedo[l] = g->G.albedo[l] > 0 ? gs[l] / g->G.albedo[l] : 0.0;
+    return DARTRAY_OK;
+}
+
+int dartray_set_kappa_rho(dartray_grid *g, const float *kappa_rho, int src_is_device) {
+    g_last_error.clear();
+    if (!g || !kappa_rho) return fail(DARTRAY_E_INVAL, "null argument");
+    int rc = set_device(g);
+    if (rc) return rc;
+    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
+    if ((rc = copy_in(g->d_kr, kappa_rho, nU, src_is_device != 0, g->stream))) return rc;
+    CK(cudaStreamSynchronize(g->stream));
+    return DARTRAY_OK;
+}
+
 int dartray_set_emissivity(dartray_grid *g, const float *emis, int src_is_device) {
     g_last_error.clear();
     if (!g || !emis) return fail(DARTRAY_E_INVAL, "null argument");

@@ -145,3 +145,192 @@ inline int launch_map(const DevGrid &G, const MapArgs &M, int blocks, cudaStream
 }
 
 }  // namespace dartray
+
+namespace dartray {
+
+// ---------------------------------------------------------- external maps
+// Orthographic surface-brightness map for an observer far away along the
+// unit vector `view` (from the model toward the observer): one line of sight
+// per pixel, parallel to -view, through the pixel centre
+// origin + (i + 1/2) px right + (j + 1/2) px up of the image plane (right =
+// up x view).  Along it the model is integrated front to back (Sect. 2,
+// end: I_obs = I_0 e^-tau, the cells as a continuous medium -- the volume
+// rendering of the paper): a cell crossed over ds with extinction kr and
+// source eta (luminosity per volume per sr toward the observer: the stellar
+// emissivity plus the total scattered luminosity of the j_sca pixel that
+// holds `view`, per its solid angle, per volume) adds
+//   E = eta (1 - e^{-kr ds}) / kr     (eta ds for kr = 0)
+// times the transmission T_front of the cells in front of it.
+// The vector-Jacobian product of the map with respect to kr (the source
+// held fixed) recomputes the transmission along each line of sight instead
+// of storing it: a first pass gives the pixel's SB, a second the prefix P
+// of the contributions, and
+//   dSB/dkr_c = T_front dE/dkr - ds (SB - P_including_c).
+struct ExtMapArgs {
+    double view[3], right[3], up[3], origin[2], px;
+    int nx, ny;
+    double box_lo[3], box_hi[3];  // the root lattice
+    const float *jsca;            // total j_sca, or null
+    float *map;                   // [nl][ny][nx] (forward)
+    const float *dmap;            // [nl][ny][nx] upstream gradient (VJP)
+    float *grad;                  // [n_leaf][nl] (VJP), accumulated
+    double *grad_sca;             // [nl] (VJP): sum of dmap times the scattered part of the map
+};
+
+// E and dE/dkr of a cell for x = kr ds (series below 1e-4, where the
+// closed forms cancel)
+__device__ inline void cell_emission(double eta, double kr, double ds, double *E, double *dE) {
+    const double x = kr * ds;
+    if (x < 1e-4) {
+        *E = eta * ds * (1.0 - x * (0.5 - x / 6.0));
+        *dE = eta * ds * ds * (-0.5 + x * (1.0 / 3.0 - x / 8.0));
+    } else {
+        const double omT = -expm1(-x);
+        *E = eta * omT / kr;
+        *dE = eta * (ds * (1.0 - omT) * kr - omT) / (kr * kr);
+    }
+}
+
+template <int NL, bool VJP>
+__global__ void __launch_bounds__(128) external_map_kernel(const DevGrid G, const ExtMapArgs M) {
+    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= M.nx * M.ny) return;
+    const int i = pix % M.nx, j = pix / M.nx;
+    const double u = M.origin[0] + (i + 0.5) * M.px, v = M.origin[1] + (j + 0.5) * M.px;
+    // the line p0 + t d, d = -view, entering the root lattice at t0
+    double p0[3], d[3];
+    for (int a = 0; a < 3; ++a) {
+        p0[a] = u * M.right[a] + v * M.up[a];
+        d[a] = -M.view[a];
+    }
+    double t0 = -1e300, t1 = 1e300;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] != 0.0) {
+            double ta = (M.box_lo[a] - p0[a]) / d[a], tb = (M.box_hi[a] - p0[a]) / d[a];
+            if (ta > tb) { const double t = ta; ta = tb; tb = t; }
+            t0 = fmax(t0, ta);
+            t1 = fmin(t1, tb);
+        } else if (p0[a] < M.box_lo[a] || p0[a] >= M.box_hi[a]) {
+            t1 = -1e300;
+        }
+    }
+    const long long npix = static_cast<long long>(M.nx) * M.ny;
+    if (!(t1 > t0)) {
+        if (!VJP)
+            for (int l = 0; l < NL; ++l) M.map[l * npix + pix] = 0.f;
+        return;
+    }
+    const float3 n = make_float3(static_cast<float>(d[0]), static_cast<float>(d[1]), static_cast<float>(d[2]));
+    // the j_sca pixel holding the direction toward the observer, per wavelength
+    int q[NL];
+    double omq[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const int kl = G.k_lam[l];
+        q[l] = static_cast<int>(vec2pix_d(kl, M.view[0], M.view[1], M.view[2]));
+        omq[l] = 4.0 * kPi / (12 << (2 * kl));
+    }
+    double SB[NL], P[NL], Tf[NL], g[NL], SBs[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        SB[l] = 0.0;
+        SBs[l] = 0.0;
+        P[l] = 0.0;
+        Tf[l] = 1.0;
+        g[l] = VJP ? static_cast<double>(M.dmap[l * npix + pix]) : 0.0;
+    }
+    for (int pass = 0; pass < (VJP ? 2 : 1); ++pass) {
+        // march front to back from the entry point (held inside the lattice:
+        // rounding must not put it outside)
+        float3 p;
+        {
+            double e[3];
+            for (int a = 0; a < 3; ++a) e[a] = fmin(fmax(p0[a] + t0 * d[a], M.box_lo[a]), M.box_hi[a]);
+            p = make_float3(static_cast<float>(e[0]), static_cast<float>(e[1]), static_cast<float>(e[2]));
+        }
+        int leaf = locate_root(G, 0, p, n);
+        double t = t0;
+        for (int guard = 0; leaf >= 0 && guard < (1 << 22); ++guard) {
+            const float4 b = __ldg(&G.leaf_box[leaf]);
+            // exit distance along the line (double, from the line's own origin)
+            double te = 1e300;
+            int tie = 0;
+            double bnd[3];
+            const double lo[3] = {b.x, b.y, b.z};
+            for (int a = 0; a < 3; ++a) {
+                bnd[a] = d[a] > 0 ? lo[a] + b.w : lo[a];
+                if (d[a] != 0.0) {
+                    const double ta = (bnd[a] - p0[a]) / d[a];
+                    if (ta < te) { te = ta; tie = 1 << a; }
+                    else if (ta == te) tie |= 1 << a;
+                }
+            }
+            const double ds = fmax(te - t, 0.0);
+            const double V = static_cast<double>(b.w) * b.w * b.w;
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                const double kr = __ldg(&G.kappa_rho[static_cast<long long>(leaf) * NL + l]);
+                double eta = __ldg(&G.emis[static_cast<long long>(leaf) * NL + l]), eta_s = 0.0;
+                if (M.jsca) {
+                    const int np = 12 << (2 * G.k_lam[l]);
+                    eta_s = static_cast<double>(M.jsca[G.off_lam[l] + static_cast<long long>(leaf) * np + q[l]]) /
+                            (omq[l] * V);
+                    eta += eta_s;
+                }
+                double E, dE;
+                cell_emission(eta, kr, ds, &E, &dE);
+                const double contrib = E * Tf[l];
+                if (pass == 0) {
+                    SB[l] += contrib;
+                    if (VJP && eta > 0.0) SBs[l] += contrib * (eta_s / eta);  // E is linear in eta
+                } else {
+                    P[l] += contrib;
+                    const double dSB = Tf[l] * dE - ds * (SB[l] - P[l]);
+                    const double gv = g[l] * dSB;
+                    if (gv != 0.0) atomicAdd(&M.grad[static_cast<long long>(leaf) * NL + l], static_cast<float>(gv));
+                }
+                Tf[l] *= exp(-kr * ds);
+            }
+            if (tie == 0 || te >= t1) break;
+            t = te;
+            // the exit point: on the faces reached exactly, elsewhere on the
+            // closed box of the cell being left
+            double e[3];
+            for (int a = 0; a < 3; ++a)
+                e[a] = ((tie >> a) & 1) ? bnd[a] : fmin(fmax(p0[a] + te * d[a], lo[a]), lo[a] + b.w);
+            const float3 pf = make_float3(static_cast<float>(e[0]), static_cast<float>(e[1]), static_cast<float>(e[2]));
+            const int nxt = next_leaf(G, leaf, tie, pf, n);
+            if (nxt == leaf) break;
+            leaf = nxt;
+        }
+        if (pass == 0 && !VJP)
+#pragma unroll
+            for (int l = 0; l < NL; ++l) M.map[l * npix + pix] = static_cast<float>(SB[l]);
+        if (pass == 0 && VJP && M.grad_sca)
+#pragma unroll
+            for (int l = 0; l < NL; ++l)
+                if (g[l] * SBs[l] != 0.0) atomicAdd(&M.grad_sca[l], g[l] * SBs[l]);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) Tf[l] = 1.0;
+    }
+}
+
+inline int launch_external_map(const DevGrid &G, const ExtMapArgs &M, bool vjp, cudaStream_t s) {
+    const int blocks = (M.nx * M.ny + 127) / 128;
+#define EXT(NLV)                                                                    \
+    do {                                                                            \
+        if (vjp) external_map_kernel<NLV, true><<<blocks, 128, 0, s>>>(G, M);       \
+        else external_map_kernel<NLV, false><<<blocks, 128, 0, s>>>(G, M);          \
+    } while (0)
+    switch (G.nl) {
+    case 1: EXT(1); return 0;
+    case 2: EXT(2); return 0;
+    case 4: EXT(4); return 0;
+    case 8: EXT(8); return 0;
+    case 16: EXT(16); return 0;
+    default: return 1;
+    }
+#undef EXT
+}
+
+}  // namespace dartray

@@ -49,6 +49,12 @@ class dartray_params(C.Structure):
 _L = MAX_LAMBDA
 
 
+class dartray_dust(C.Structure):
+    _fields_ = [("n_ir", C.c_int32), ("lam_ir", C.c_double * MAX_LAMBDA), ("dlam_ir", C.c_double * MAX_LAMBDA),
+                ("n_stellar", C.c_int32), ("dlam_stellar", C.c_double * MAX_LAMBDA), ("scale", C.c_double),
+                ("t_min", C.c_double), ("t_max", C.c_double)]
+
+
 class dartray_stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("rays", "crossings", "splits", "merges", "blocks", "escapes",
                                           "cuts", "lows", "resumes", "waves", "sources")] + \
@@ -102,6 +108,13 @@ def load(build_if_missing=True):
         "dartray_model_info": ([P, C.c_int32, P, P, P, P, P], C.c_int),
         "dartray_model_stats": ([P, C.c_int32, P], C.c_int),
         "dartray_autotune": ([P, C.c_int32, P, P], C.c_int),
+        "dartray_dust_emission": ([P, P, P, P, P, C.c_int, P], C.c_int),
+        "dartray_set_emissivity": ([P, P, C.c_int], C.c_int),
+        "dartray_direct_incremental": ([P, P], C.c_int),
+        "dartray_map_external": ([P, P, P, P, C.c_double, C.c_int32, C.c_int32, C.c_int32, P, C.c_int], C.c_int),
+        "dartray_map_external_vjp": ([P, P, P, P, C.c_double, C.c_int32, C.c_int32, C.c_int32, P, P, P, C.c_int],
+                                     C.c_int),
+        "dartray_set_kappa_rho": ([P, P, C.c_int], C.c_int),
         "dartray_state_load": ([P, C.c_char_p], C.c_int),
         "dartray_grid_destroy": ([P], None),
         "dartray_last_error": ([], C.c_char_p),
@@ -117,7 +130,9 @@ def load(build_if_missing=True):
 EXPORTED = ("dartray_params_default", "dartray_grid_create", "dartray_direct", "dartray_scatter_iter",
             "dartray_rfed", "dartray_jsca_layout", "dartray_jsca", "dartray_map", "dartray_map_noalloc",
             "dartray_state_save", "dartray_state_load", "dartray_grid_destroy", "dartray_last_error",
-            "dartray_grid_create_batch", "dartray_model_info", "dartray_model_stats", "dartray_autotune")
+            "dartray_grid_create_batch", "dartray_model_info", "dartray_model_stats", "dartray_autotune",
+            "dartray_dust_emission", "dartray_set_emissivity", "dartray_direct_incremental",
+            "dartray_map_external", "dartray_map_external_vjp", "dartray_set_kappa_rho")
 
 
 def _check(rc):
@@ -355,6 +370,74 @@ class DartRay:
         dartray_map(self._h, observer, nside_k, max_sub, use_jsca, _ptr(out), dev)
         return out
 
+    @staticmethod
+    def _frame(view, up, origin):
+        d3 = C.c_double * 3
+        return d3(*map(float, view)), d3(*map(float, up)), (C.c_double * 2)(*map(float, origin))
+
+    def map_external(self, view, up, origin, pixel, nx, ny, use_jsca=True, out=None):
+        """Orthographic map for a distant observer (dartray_map_external):
+        [n_lambda][ny][nx], into `out` (host array or CUDA tensor) if given."""
+        if out is None:
+            out = np.empty((self.n_lambda, ny, nx), np.float32)
+        v, u, o = self._frame(view, up, origin)
+        _check(load().dartray_map_external(self._h, v, u, o, float(pixel), int(nx), int(ny), int(bool(use_jsca)),
+                                           _ptr(out), int(_is_cuda_tensor(out))))
+        return out
+
+    def map_external_vjp(self, view, up, origin, pixel, nx, ny, dmap, use_jsca=True, out=None, with_albedo=False):
+        """d/d kappa_rho of sum(dmap * map) (dartray_map_external_vjp):
+        [n_leaf][n_lambda]; dmap and out both host arrays or both CUDA
+        tensors.  with_albedo: also return d/d albedo [n_lambda] (float64)."""
+        dev = _is_cuda_tensor(dmap)
+        if dev:
+            dmap = dmap.contiguous()
+            if out is None:
+                import torch
+                out = torch.empty((self.n_leaf, self.n_lambda), dtype=torch.float32, device=dmap.device)
+        else:
+            dmap = np.ascontiguousarray(dmap, np.float32)
+            if out is None:
+                out = np.empty((self.n_leaf, self.n_lambda), np.float32)
+        v, u, o = self._frame(view, up, origin)
+        ga = np.zeros(self.n_lambda, np.float64)
+        _check(load().dartray_map_external_vjp(self._h, v, u, o, float(pixel), int(nx), int(ny), int(bool(use_jsca)),
+                                               _ptr(dmap), _ptr(out), _ptr(ga), int(dev)))
+        return (out, ga) if with_albedo else out
+
+    def set_kappa_rho(self, kr):
+        k = kr.contiguous() if _is_cuda_tensor(kr) else np.ascontiguousarray(kr, np.float32)
+        _check(load().dartray_set_kappa_rho(self._h, _ptr(k), int(_is_cuda_tensor(k))))
+
+    def set_emissivity(self, emis):
+        e = emis.contiguous() if _is_cuda_tensor(emis) else np.ascontiguousarray(emis, np.float32)
+        _check(load().dartray_set_emissivity(self._h, _ptr(e), int(_is_cuda_tensor(e))))
+
+    def direct_incremental(self):
+        st = dartray_stats()
+        _check(load().dartray_direct_incremental(self._h, C.byref(st)))
+        self.last_stats = st.to_dict(self.n_lambda)
+        return self.last_stats
+
+    def dust_emission(self, stellar, lam_ir, dlam_ir, dlam_stellar, scale, t_min=2.0, t_max=5000.0):
+        """Dust emission of this (dust) grid heated by the absorbed light of
+        both grids (dartray_dust_emission): returns T [n_leaf], j [n_leaf][n_ir]
+        and the largest relative change of j since the previous call; the
+        grid's emissivity becomes that change."""
+        d = dartray_dust()
+        d.n_ir = self.n_lambda
+        d.n_stellar = stellar.n_lambda
+        for i in range(self.n_lambda):
+            d.lam_ir[i], d.dlam_ir[i] = float(lam_ir[i]), float(dlam_ir[i])
+        for i in range(stellar.n_lambda):
+            d.dlam_stellar[i] = float(dlam_stellar[i])
+        d.scale, d.t_min, d.t_max = float(scale), float(t_min), float(t_max)
+        T = np.empty(self.n_leaf, np.float32)
+        j = np.empty((self.n_leaf, self.n_lambda), np.float32)
+        rel = C.c_double()
+        _check(load().dartray_dust_emission(self._h, stellar._h, C.byref(d), _ptr(T), _ptr(j), 0, C.byref(rel)))
+        return T, j, rel.value
+
     def save(self, path):
         dartray_state_save(self._h, path)
 
@@ -401,3 +484,57 @@ class DartRayBatch(DartRay):
         blk = self.jsca_block(l, which)
         a = self.info[m]["leaf_offset"]
         return blk[a:a + self.info[m]["n_leaf"]]
+
+
+def dust_self_heating(stellar, dust, lam_ir, dlam_ir, dlam_stellar, scale, f_l=0.01, tol=0.01, max_steps=20,
+                      max_iters=12):
+    """The dust emission RT with self-heating (Sect. 3.3): ``stellar`` has run
+    its sweep; ``dust`` is a grid of the same topology at the dust
+    wavelengths.  Step 1: the emission heated by the stellar light alone;
+    step 2: its full RT (steps 1-2 of Sect. 2 and scattering iterations to
+    f_l); then, until the emission changes by less than ``tol`` everywhere,
+    the emission is recomputed with the absorbed dust light added and only
+    its change is propagated (no U_LL step; U and j_sca continue).  Returns
+    the per-step history (largest relative change, crossings)."""
+    hist = []
+    T, j, rel = dust.dust_emission(stellar, lam_ir, dlam_ir, dlam_stellar, scale)
+    st = dust.direct()
+    for step in range(max_steps):
+        cross = st["crossings"]
+        for _ in range(max_iters):
+            rem, s2 = dust.scatter_iter()
+            cross += s2["crossings"]
+            if rem < f_l:
+                break
+        T, j, rel = dust.dust_emission(stellar, lam_ir, dlam_ir, dlam_stellar, scale)
+        hist.append(dict(step=step, max_rel_change=rel, crossings=cross))
+        if rel < tol:
+            break
+        st = dust.direct_incremental()
+    return T, j, hist
+
+
+def external_map(model, kappa_rho, view, up, origin, pixel, nx, ny, use_jsca=True):
+    """Differentiable orthographic map: kappa_rho (CUDA tensor [n_leaf][n_lambda])
+    -> map [n_lambda][ny][nx] of `model` (a DartRay), the source (emissivity and
+    j_sca of the last sweep) held fixed.  Forward and backward are the
+    library's map kernel and its reverse march."""
+    import torch
+
+    class _ExternalMap(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, kr):
+            kr = kr.detach().contiguous()
+            model.set_kappa_rho(kr)
+            out = torch.empty((model.n_lambda, ny, nx), dtype=torch.float32, device=kr.device)
+            model.map_external(view, up, origin, pixel, nx, ny, use_jsca, out=out)
+            ctx.save_for_backward(kr)
+            return out
+
+        @staticmethod
+        def backward(ctx, g):
+            (kr,) = ctx.saved_tensors
+            model.set_kappa_rho(kr)  # the medium the forward map saw
+            return model.map_external_vjp(view, up, origin, pixel, nx, ny, g.float().contiguous(), use_jsca)
+
+    return _ExternalMap.apply(kappa_rho)

@@ -126,7 +126,7 @@ def _c_layout(struct, fields, tmp_path):
     return vals[0], vals[1:]
 
 
-@pytest.mark.parametrize("cls", [dr.dartray_grid_desc, dr.dartray_params, dr.dartray_stats],
+@pytest.mark.parametrize("cls", [dr.dartray_grid_desc, dr.dartray_params, dr.dartray_stats, dr.dartray_dust],
                          ids=lambda c: c.__name__)
 def test_binding_structs_match_the_header_layout(cls, tmp_path):
     """The ctypes mirrors of the ABI structs have the header's size and the
