@@ -62,6 +62,37 @@ def bytes_per_crossing(nl):
 # a deposit record: cell (4 B) and the ray direction with the HG coefficient (16 B)
 RECORD_BYTES = 20
 
+# DRAM and L2 bytes per crossing of the marcher, summed over all its launches
+# of the 1/30000-source case and divided by that case's crossings (ncu:
+# profiles/march_kernel_traffic_galaxy3e5_subset30000.md); a full-size
+# launch's traffic is taken as these times its crossings.
+MARCH_DRAM_BYTES_PER_CROSSING = None
+MARCH_L2_BYTES_PER_CROSSING = None
+
+
+def l2_copy_gbs():
+    """Measured L2 bandwidth: a device-to-device copy of 24 MiB (read +
+    write 48 MiB, resident in the 129 MB L2), best of 20 timed batches of 20
+    copies."""
+    import torch
+    a = torch.empty(6 << 20, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    a.fill_(1.0)
+    for _ in range(10):
+        b.copy_(a)
+    best = None
+    for _ in range(20):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    return 20 * 2 * a.numel() * 4 / best / 1e9
+
 
 def make_workload():
     import synth
@@ -523,8 +554,20 @@ def main():
         # includes any wait for SMs held by the other pipeline's kernels)
         march_sum_ms, launches = prof["march_sum_ms"], prof["march_launches"]
         achieved = alg_bytes / (march_sum_ms / 1e3) / 1e9 if march_sum_ms > 0 else None
+        per_launch = prof["march_crossings"] / launches if launches else 0.0
+        traffic = MARCH_DRAM_BYTES_PER_CROSSING * per_launch if MARCH_DRAM_BYTES_PER_CROSSING else None
+        l2 = None
+        if MARCH_L2_BYTES_PER_CROSSING and march_sum_ms > 0:
+            l2_peak = l2_copy_gbs()
+            l2_ach = MARCH_L2_BYTES_PER_CROSSING * prof["march_crossings"] / (march_sum_ms / 1e3) / 1e9
+            l2 = {"achieved": l2_ach, "peak": l2_peak, "unit": "GB/s", "frac": l2_ach / l2_peak,
+                  "bytes_per_crossing": MARCH_L2_BYTES_PER_CROSSING,
+                  "peak_source": "measured here: L2-resident device copy (48 MiB moved per copy)"}
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": (achieved / peak) if achieved else None, "traffic": None,
+                    "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                    "traffic_note": "ncu DRAM bytes per crossing of the small case times the crossings of an "
+                                    "average full-size launch" if traffic else None,
+                    "l2": l2,
                     "kernel": "march_kernel (ray marcher)", "peak_source": peak_src,
                     "launches": launches, "avg_launch_ms": march_sum_ms / launches if launches else None,
                     "bytes_per_crossing": bytes_per_crossing(nl), "record_bytes": RECORD_BYTES,

@@ -288,17 +288,36 @@ int dartray_map_external(dartray_grid *grid, const double view[3], const double 
                          double pixel, int32_t nx, int32_t ny, int32_t use_jsca, float *map, int dst_is_device);
 
 /* Vector-Jacobian product of dartray_map_external, the radiation field of
- * the last sweep held fixed: grad_kappa_rho[c][l] = sum over pixels of
- * dmap[l][pixel] d map[l][pixel] / d kappa_rho[c][l] (the source eta held
- * fixed), and grad_albedo[l] = the same for the albedo, through j_sca, which
- * is proportional to it at a fixed radiation field (null: not wanted).  The
- * transmission is recomputed along every line of sight (two passes) instead
- * of stored.  dmap [n_lambda][ny][nx] and grad_kappa_rho [n_leaf][n_lambda]
- * are both host or both device memory; grad_albedo [n_lambda] is host
- * memory.  Errors: INVAL, CUDA. */
+ * the last sweep held fixed (the luminosity each crossing deposits into the
+ * scattering source function does not move):
+ *   grad_kappa_rho[c][l] = sum over pixels of dmap[l][pixel]
+ *                          d map[l][pixel] / d kappa_rho[c][l]
+ * (the source eta held fixed);
+ *   grad_albedo[l], the same for the albedo, through j_sca, which is
+ * proportional to it at a fixed radiation field (null: not wanted);
+ *   grad_g[l], the same for the HG asymmetry g, through the j_sca pixel
+ * toward the observer, from the tally of dartray_jsca_dg_arm (armed for this
+ * view before dartray_direct; use_jsca set; null: not wanted; else STATE).
+ * The transmission is recomputed along every line of sight (two passes)
+ * instead of stored.  dmap [n_lambda][ny][nx] and grad_kappa_rho
+ * [n_leaf][n_lambda] are both host or both device memory; grad_albedo and
+ * grad_g [n_lambda] are host memory.  Errors: INVAL, STATE, CUDA. */
 int dartray_map_external_vjp(dartray_grid *grid, const double view[3], const double up[3], const double origin[2],
                              double pixel, int32_t nx, int32_t ny, int32_t use_jsca, const float *dmap,
-                             float *grad_kappa_rho, double *grad_albedo, int on_device);
+                             float *grad_kappa_rho, double *grad_albedo, double *grad_g, int on_device);
+
+/* Arm (view non-null) or disarm (null) the tally of d j_sca / d g: from the
+ * next dartray_direct on, every deposit into the scattering source function
+ * (Eq. 4 with the HG function, rows normalised over the pixels) also adds
+ * L_sca d/dg [Phi(n_v.n) / sum_q Phi(n_q.n)] to its cell, n_v the centre of
+ * the j_sca pixel holding `view` (per wavelength), L_sca held fixed.  The
+ * tally covers step 2 and the scattering iterations.  Single-model grids
+ * outside the octant mode.  Errors: INVAL, CUDA. */
+int dartray_jsca_dg_arm(dartray_grid *grid, const double view[3]);
+
+/* The armed tally [n_leaf][n_lambda] (host or device).  Errors: INVAL,
+ * STATE (not armed), CUDA. */
+int dartray_jsca_dg(dartray_grid *grid, float *out, int dst_is_device);
 
 /* Replace kappa_rho [n_leaf][n_lambda] (host or device), e.g. to map a
  * changed dust distribution; the RFED and j_sca keep their values until the

@@ -104,6 +104,11 @@ typedef struct {
     double L_sca2;            /* total scattered luminosity at the end of step 2 */
     double f_u;               /* f_U of the last phase */
     int32_t n_src;            /* N_s of the last phase */
+    /* optional: d/dg_l of the total j_sca pixel holding dg_view, per cell,
+     * with the deposited luminosities held fixed ([n_leaf][nl]; dg_on = 1) */
+    double *dg;
+    double dg_view[3];
+    int32_t dg_on;
 } or_state;
 
 /* ------------------------------------------------------------------ HEALPix */
@@ -244,6 +249,13 @@ int64_t or_vec2pix(int k, const double v[3]) {
 double or_hg(double g, double mu) {
     const double x = 1.0 + g * g - 2.0 * g * mu;
     return (1.0 - g * g) / (4.0 * OR_PI * x * sqrt(x));
+}
+
+/* d Phi / d g of the HG function above (quotient rule on (1 - g^2) x^(-3/2)
+ * with dx/dg = 2g - 2mu). */
+double or_hg_dg(double g, double mu) {
+    const double x = 1.0 + g * g - 2.0 * g * mu;
+    return (-2.0 * g * x - 1.5 * (1.0 - g * g) * (2.0 * g - 2.0 * mu)) / (4.0 * OR_PI * x * x * sqrt(x));
 }
 
 /* Eq. 5 before rounding.  theta_min = FWHM[Phi - Phi(pi)] / n_FWHM; the half
@@ -486,15 +498,19 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
     S->counters[CT_RAYS]++;
     /* HG normalisation for this ray direction (reading: rows normalised so
      * that the discrete phase function conserves the scattered luminosity). */
-    double Z[OR_MAXL];
+    double Z[OR_MAXL], Zg[OR_MAXL];
     if (C->mode != 0) {
         for (int l = 0; l < nl; ++l) {
             const int npx = 12 << (2 * S->k_lam[l]);
             const double *pd = C->pixdir[S->k_lam[l]];
-            double z = 0;
-            for (int q = 0; q < npx; ++q)
-                z += or_hg(G->g[l], pd[3 * q] * n[0] + pd[3 * q + 1] * n[1] + pd[3 * q + 2] * n[2]);
+            double z = 0, zg = 0;
+            for (int q = 0; q < npx; ++q) {
+                const double mu = pd[3 * q] * n[0] + pd[3 * q + 1] * n[1] + pd[3 * q + 2] * n[2];
+                z += or_hg(G->g[l], mu);
+                if (S->dg_on) zg += or_hg_dg(G->g[l], mu);
+            }
             Z[l] = z;
+            Zg[l] = zg;
         }
     }
     if (leaf < 0) {  /* starts outside the model */
@@ -605,6 +621,12 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
                         for (int q = 0; q < npx; ++q) {
                             const double mu = pd[3 * q] * n[0] + pd[3 * q + 1] * n[1] + pd[3 * q + 2] * n[2];
                             row[q] += sca * or_hg(G->g[l], mu) / Z[l];
+                        }
+                        if (S->dg_on) {  /* d/dg of the weight Phi_q / Z of the view pixel */
+                            const int64_t qv = or_vec2pix(kl, S->dg_view);
+                            const double mu = pd[3 * qv] * n[0] + pd[3 * qv + 1] * n[1] + pd[3 * qv + 2] * n[2];
+                            S->dg[(int64_t)leaf * nl + l] +=
+                                sca * (or_hg_dg(G->g[l], mu) - or_hg(G->g[l], mu) * Zg[l] / Z[l]) / Z[l];
                         }
                     }
                 }
@@ -794,6 +816,7 @@ static int or_mirrors(const or_grid *G, const double *leaf_box, const double cen
  * Sect. 3.3 process only the change of the dust emission).  Returns 0 or a
  * negative error. */
 static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode, int keep_U) {
+    if (P->octant && S->dg_on) return -7;  /* the g tally is not folded over mirror images */
     const int nl = G->n_lambda;
     or_ctx C;
     memset(&C, 0, sizeof C);
@@ -1023,6 +1046,7 @@ int or_direct(const or_grid *G, const or_params *P, or_state *S) {
     S->cur_is_a = 1;  /* deposits of step 2 go to pend_b (the "next" buffer) */
     memset(S->counters, 0, sizeof S->counters);  /* counters cover one call */
     memset(S->jsca_total, 0, sizeof(double) * (size_t)S->sca_len);
+    if (S->dg_on) memset(S->dg, 0, sizeof(double) * (size_t)G->n_leaf * G->n_lambda);
     int rc = or_phase(G, P, S, 0, 0);
     if (rc) return rc;
     return or_phase(G, P, S, 1, 0);

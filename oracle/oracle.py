@@ -86,7 +86,8 @@ class _State(C.Structure):
                 ("U", C.c_void_p), ("U_LL", C.c_void_p), ("pend_a", C.c_void_p),
                 ("pend_b", C.c_void_p), ("cur_is_a", C.c_int32), ("jsca_total", C.c_void_p),
                 ("ledger", (C.c_double * 7) * MAXL), ("counters", C.c_int64 * 11),
-                ("L_sca2", C.c_double), ("f_u", C.c_double), ("n_src", C.c_int32)]
+                ("L_sca2", C.c_double), ("f_u", C.c_double), ("n_src", C.c_int32),
+                ("dg", C.c_void_p), ("dg_view", C.c_double * 3), ("dg_on", C.c_int32)]
 
 
 _variants = {}
@@ -268,7 +269,8 @@ class OracleError(RuntimeError):
 
 _ERRORS = {-1: "out of memory", -2: "crossing cap reached", -3: "wave cap reached",
            -4: "source cell not found", -5: "no progress across a face (inexact grid coordinates)",
-           -6: "octant mode: the model is not mirror-symmetric about its centre"}
+           -6: "octant mode: the model is not mirror-symmetric about its centre",
+           -7: "the g tally is not available in the octant mode"}
 
 
 class Oracle:
@@ -316,6 +318,20 @@ class Oracle:
 
     def direct(self):
         self._check(self._lib.or_direct(self._g.ref, C.byref(self._p), C.byref(self._s)))
+
+    def dg_arm(self, view):
+        """From the next direct() on, accumulate per cell and wavelength the
+        derivative with respect to g of the total j_sca pixel holding `view`
+        (the deposited luminosities held fixed); dg() returns it."""
+        w = np.asarray(view, np.float64) / np.linalg.norm(view)
+        self.dg_buf = np.zeros(self.grid.n_leaf * self.grid.n_lambda)
+        self._s.dg = self.dg_buf.ctypes.data
+        for a in range(3):
+            self._s.dg_view[a] = w[a]
+        self._s.dg_on = 1
+
+    def dg(self):
+        return self.dg_buf.reshape(self.grid.n_leaf, self.grid.n_lambda)
 
     def direct_incremental(self):
         """Step 2 for a change of the emissivity, on top of the current U and
@@ -555,6 +571,17 @@ class ExternalMapOracle:
         finally:
             self.eta = saved
         return m
+
+    def vjp_g(self, dmap, dg, kr=None):
+        """d/d g_l of sum(dmap * map), the radiation field held fixed: the
+        map of the source dg / (Omega V) (dg: the oracle's tally for this
+        view, [n_leaf][n_lambda])."""
+        g = self.g
+        V = g.leaf_size.astype(np.float64) ** 3
+        src = np.zeros((g.n_leaf, g.n_lambda))
+        for l in range(g.n_lambda):
+            src[:, l] = dg[:, l] / (4 * np.pi / (12 * 4 ** self.o.k_lam[l])) / V
+        return (dmap * self.map(kr, eta=src)).sum(axis=(1, 2))
 
     def vjp_albedo(self, dmap, kr=None):
         """d/d albedo_l of sum(dmap * map), the radiation field held fixed:

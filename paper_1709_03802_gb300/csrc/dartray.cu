@@ -67,6 +67,9 @@ int k_hp_host(double g, int n_fwhm, int cap) {
 
 constexpr int kPipes = 2;
 constexpr int kMaxModels = 4096;
+// two-pass segment sums: at most kSegParts parts per segment, kSegPartial partial sums in all
+constexpr int kSegParts = 512;
+constexpr int kSegPartial = 8192;
 
 // Map staging buffer of dartray_map_noalloc: a fixed device array (8 MiB), so
 // that entry point needs no allocation.  Every device that loads the library
@@ -162,7 +165,7 @@ struct dartray_grid {
     double *d_mled = nullptr;
     unsigned long long *d_mled_fix = nullptr;
     long long *d_seg_beg = nullptr, *d_seg_len = nullptr;  // (model, wavelength) blocks of the j_sca array
-    double *d_seg_out = nullptr;
+    double *d_seg_out = nullptr, *d_seg_part = nullptr;
     int march_smem = 0;
     std::vector<long long> m_leaf0, m_point0;
     std::vector<int> m_nleaf;
@@ -171,6 +174,12 @@ struct dartray_grid {
     std::vector<double> m_ledger;  // [n_models][LG_N][nl] of the last phase of the last call
     float *d_jd = nullptr;         // dust emission of the last dartray_dust_emission call
     unsigned *d_maxrel = nullptr;
+    // d j_sca / d g tally for one view (dartray_jsca_dg_arm): the total since
+    // dartray_direct, the current phase's part, the view pixels' directions
+    bool dg_on = false, dg_phase_live = false;
+    double dg_view[3] = {0.0, 0.0, 0.0};
+    float *d_dg = nullptr, *d_dg_phase = nullptr;
+    float4 *d_dg_dir = nullptr;
     Exps eU{}, eJ{}, eL{};
     double *d_partial = nullptr, *h_partial = nullptr;  // deterministic sums
 };
@@ -184,8 +193,8 @@ void free_all(dartray_grid *g) {
                     g->d_src_pos, g->d_src_S, g->d_st, g->d_sum, g->d_stage, g->d_Ufix, g->d_pfix,
                     g->d_partial, g->d_mirror, g->d_mirror_pix, g->d_oct_u, g->d_oct_p, g->d_thr,
                     g->d_fu_model, g->d_models, g->d_leaf_model, g->d_point_model, g->d_model_active,
-                    g->d_mcount, g->d_mled, g->d_mled_fix, g->d_seg_beg, g->d_seg_len, g->d_seg_out,
-                    g->d_jd, g->d_maxrel};
+                    g->d_mcount, g->d_mled, g->d_mled_fix, g->d_seg_beg, g->d_seg_len, g->d_seg_out, g->d_seg_part,
+                    g->d_jd, g->d_maxrel, g->d_dg, g->d_dg_phase, g->d_dg_dir};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kPipes; ++i) {
@@ -308,6 +317,11 @@ int enqueue_flush_kernels(dartray_grid *g, Pipe &P, float *pend_dst, int force) 
     scan_blocks_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, reinterpret_cast<const int *>(P.d_cnt), g->n_leaf, P.d_blocksum);
     scan_offsets_kernel<<<1, 1, 0, s>>>(P.d_pd, P.d_blocksum, nb, P.d_total);
     scan_apply_kernel<<<nb, kBlock, 0, s>>>(P.d_pd, P.d_cnt, g->n_leaf, P.d_blocksum, P.d_off, P.d_cur);
+    if (g->dg_on && g->dg_phase_live) {
+        dg_tally_kernel<<<gb, kBlock, 0, s>>>(g->G, P.d_pd, P.d_rec_n, P.d_rec_cell, P.d_rec_dir, P.d_rec_coef,
+                                              g->rec_cap, g->d_dg_dir, g->d_dg_phase);
+        ++g->launches;
+    }
     rec_scatter_kernel<<<gb, kBlock, 0, s>>>(P.d_pd, P.d_rec_n, P.d_rec_cell, P.d_rec_dir, P.d_rec_coef, g->rec_cap,
                                              g->nl, P.d_cur, P.d_srt_dir, P.d_srt_coef);
     FlushArgs F{};
@@ -644,6 +658,9 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res, bool keep_U = false) 
     base.max_cross = g->P.max_cross;
     base.st = g->d_st;
     base.rec_cap = g->rec_cap;
+    g->dg_phase_live = g->dg_on && mode != MODE_LL;
+    base.dg = g->dg_phase_live ? g->d_dg_phase : nullptr;
+    base.dg_dir = g->d_dg_dir;
     const bool det = g->P.deterministic != 0;
     if (det) {
         // Fixed-point exponents from the luminosity L_emit the phase emits
@@ -717,6 +734,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res, bool keep_U = false) 
                 CK(cudaMemcpyAsync(g->d_U, g->d_ULL, nU * sizeof(float), cudaMemcpyDeviceToDevice, s));
             }
             CK(cudaMemsetAsync(pend_dst, 0, g->sca_len * sizeof(float), s));
+            if (g->dg_phase_live) CK(cudaMemsetAsync(g->d_dg_phase, 0, nU * sizeof(float), s));
         }
         if (det) {
             CK(cudaMemsetAsync(g->d_Ufix, 0, nU * sizeof(unsigned long long), s));
@@ -947,14 +965,23 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res, bool keep_U = false) 
     if (mode != MODE_LL) {
         add_pending_kernel<<<8 * g->num_sms, kBlock, 0, s>>>(pend_dst, g->d_jtot, g->sca_len);
         ++g->launches;
+        if (g->dg_phase_live) {
+            add_pending_kernel<<<8 * g->num_sms, kBlock, 0, s>>>(g->d_dg_phase, g->d_dg, static_cast<long long>(nU));
+            ++g->launches;
+        }
+        g->dg_phase_live = false;
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(g->d_ULL, g->d_U, nU * sizeof(float), cudaMemcpyDeviceToDevice, s));
         // remaining scattered luminosity per model (sum over its wavelength
         // blocks), in a fixed order
         const int nseg = g->n_models * g->nl;
         std::vector<double> seg(nseg);
-        segment_sum_kernel<<<nseg, kBlock, 0, s>>>(pend_dst, g->d_seg_beg, g->d_seg_len, g->d_seg_out);
-        ++g->launches;
+        const int parts = std::max(1, std::min(kSegParts, kSegPartial / nseg));
+        segment_partial_kernel<<<dim3(nseg, parts), kBlock, 0, s>>>(pend_dst, g->d_seg_beg, g->d_seg_len, parts,
+                                                                     g->d_seg_part);
+        segment_finish_kernel<<<(nseg + kBlock - 1) / kBlock, kBlock, 0, s>>>(g->d_seg_part, nseg, parts,
+                                                                              g->d_seg_out);
+        g->launches += 2;
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(seg.data(), g->d_seg_out, nseg * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1268,6 +1295,7 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
     AL(g->d_seg_beg, static_cast<size_t>(n_models) * nl);
     AL(g->d_seg_len, static_cast<size_t>(n_models) * nl);
     AL(g->d_seg_out, static_cast<size_t>(n_models) * nl);
+    AL(g->d_seg_part, std::max<size_t>(static_cast<size_t>(n_models) * nl, kSegPartial));
     if (n_models > 1) {
         AL(g->d_models, n_models);
         AL(g->d_leaf_model, tot_leaf);
@@ -1483,6 +1511,7 @@ int dartray_direct(dartray_grid *g, dartray_stats *stats) {
     if (rc) return rc;
     CK(cudaMemsetAsync(g->d_st, 0, sizeof(DevStats), g->stream));
     CK(cudaMemsetAsync(g->d_jtot, 0, g->sca_len * sizeof(float), g->stream));
+    if (g->dg_on) CK(cudaMemsetAsync(g->d_dg, 0, static_cast<size_t>(g->n_leaf) * g->nl * sizeof(float), g->stream));
     g->cur = 0;  // step 2 deposits into d_pend[1]
     const long long l0 = g->launches;
     g->march_ms = g->flush_ms = g->busy_ms = g->march_sum_ms = 0.0;
@@ -1620,17 +1649,23 @@ int dartray_map_external(dartray_grid *g, const double view[3], const double up[
 
 int dartray_map_external_vjp(dartray_grid *g, const double view[3], const double up[3], const double origin[2],
                              double pixel, int32_t nx, int32_t ny, int32_t use_jsca, const float *dmap,
-                             float *grad_kappa_rho, double *grad_albedo, int on_device) {
+                             float *grad_kappa_rho, double *grad_albedo, double *grad_g, int on_device) {
     g_last_error.clear();
     if (!g || !view || !up || !origin || !dmap || !grad_kappa_rho) return fail(DARTRAY_E_INVAL, "null argument");
     ExtMapArgs M{};
     int rc = external_frame(g, view, up, origin, pixel, nx, ny, &M);
     if (rc) return rc;
+    if (grad_g) {
+        bool same = g->dg_on && use_jsca;
+        for (int a = 0; a < 3; ++a) same = same && std::fabs(M.view[a] - g->dg_view[a]) <= 1e-12;
+        if (!same) return fail(DARTRAY_E_STATE, "grad_g needs use_jsca and the j_sca g tally armed for this view");
+    }
     if ((rc = set_device(g))) return rc;
     const size_t n = static_cast<size_t>(nx) * ny * g->nl, nU = static_cast<size_t>(g->n_leaf) * g->nl;
-    // the grid's staging buffer holds the per-wavelength sums (doubles, at
-    // its start) and, for host arguments, the upstream gradient and the result
-    const size_t n_dbl = 2 * kMaxLambda;  // in floats
+    // the grid's staging buffer holds the per-wavelength sums (two rows of
+    // doubles, at its start) and, for host arguments, the upstream gradient
+    // and the result
+    const size_t n_dbl = 4 * kMaxLambda;  // in floats
     float *st = nullptr;
     if ((rc = stage_buffer(g, n_dbl + (on_device ? 0 : n + nU), &st))) return rc;
     double *d_gs = reinterpret_cast<double *>(st);
@@ -1641,21 +1676,67 @@ int dartray_map_external_vjp(dartray_grid *g, const double view[3], const double
         CK(cudaMemcpyAsync(d_in, dmap, n * sizeof(float), cudaMemcpyHostToDevice, g->stream));
     }
     CK(cudaMemsetAsync(d_out, 0, nU * sizeof(float), g->stream));
-    CK(cudaMemsetAsync(d_gs, 0, kMaxLambda * sizeof(double), g->stream));
+    CK(cudaMemsetAsync(d_gs, 0, 2 * kMaxLambda * sizeof(double), g->stream));
     M.jsca = use_jsca ? g->d_jtot : nullptr;
     M.dmap = d_in;
     M.grad = d_out;
     M.grad_sca = d_gs;
+    M.dg = grad_g ? g->d_dg : nullptr;
+    M.grad_g = grad_g ? d_gs + kMaxLambda : nullptr;
     if (launch_external_map(g->G, M, true, g->stream)) return fail(DARTRAY_E_INVAL, "unsupported n_lambda");
     ++g->launches;
     CK(cudaGetLastError());
     if (!on_device) CK(cudaMemcpyAsync(grad_kappa_rho, d_out, nU * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
-    double gs[kMaxLambda];
-    CK(cudaMemcpyAsync(gs, d_gs, g->nl * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    double gs[2 * kMaxLambda];
+    CK(cudaMemcpyAsync(gs, d_gs, 2 * kMaxLambda * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     // j_sca is proportional to the albedo (the radiation field held fixed)
     if (grad_albedo)
         for (int l = 0; l < g->nl; ++l) grad_albedo[l] = g->G.albedo[l] > 0 ? gs[l] / g->G.albedo[l] : 0.0;
+    if (grad_g)
+        for (int l = 0; l < g->nl; ++l) grad_g[l] = gs[kMaxLambda + l];
+    return DARTRAY_OK;
+}
+
+int dartray_jsca_dg_arm(dartray_grid *g, const double view[3]) {
+    g_last_error.clear();
+    if (!g) return fail(DARTRAY_E_INVAL, "null grid");
+    if (!view) {
+        g->dg_on = false;
+        return DARTRAY_OK;
+    }
+    if (g->n_models > 1 || g->G.octant)
+        return fail(DARTRAY_E_INVAL, "the g tally is for single-model grids outside the octant mode");
+    const double vn = std::sqrt(view[0] * view[0] + view[1] * view[1] + view[2] * view[2]);
+    if (!(vn > 0)) return fail(DARTRAY_E_INVAL, "bad view direction");
+    int rc = set_device(g);
+    if (rc) return rc;
+    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
+    if (!g->d_dg) {
+        CK(cudaMalloc(reinterpret_cast<void **>(&g->d_dg), nU * sizeof(float)));
+        CK(cudaMalloc(reinterpret_cast<void **>(&g->d_dg_phase), nU * sizeof(float)));
+        CK(cudaMalloc(reinterpret_cast<void **>(&g->d_dg_dir), kMaxLambda * sizeof(float4)));
+    }
+    for (int a = 0; a < 3; ++a) g->dg_view[a] = view[a] / vn;
+    dg_dir_kernel<<<1, kMaxLambda, 0, g->stream>>>(g->G, g->dg_view[0], g->dg_view[1], g->dg_view[2], g->d_dg_dir);
+    ++g->launches;
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(g->d_dg, 0, nU * sizeof(float), g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    g->dg_on = true;
+    return DARTRAY_OK;
+}
+
+int dartray_jsca_dg(dartray_grid *g, float *out, int dst_is_device) {
+    g_last_error.clear();
+    if (!g || !out) return fail(DARTRAY_E_INVAL, "null argument");
+    if (!g->dg_on) return fail(DARTRAY_E_STATE, "the g tally is not armed");
+    int rc = set_device(g);
+    if (rc) return rc;
+    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
+    CK(cudaMemcpyAsync(out, g->d_dg, nU * sizeof(float), dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       g->stream));
+    CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
 }
 

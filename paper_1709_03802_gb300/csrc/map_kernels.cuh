@@ -175,6 +175,8 @@ struct ExtMapArgs {
     const float *dmap;            // [nl][ny][nx] upstream gradient (VJP)
     float *grad;                  // [n_leaf][nl] (VJP), accumulated
     double *grad_sca;             // [nl] (VJP): sum of dmap times the scattered part of the map
+    const float *dg;              // [n_leaf][nl] d j_sca(view pixel) / d g, or null (VJP)
+    double *grad_g;               // [nl] (VJP with dg): sum of dmap times d map / d g
 };
 
 // E and dE/dkr of a cell for x = kr ds (series below 1e-4, where the
@@ -230,11 +232,12 @@ __global__ void __launch_bounds__(128) external_map_kernel(const DevGrid G, cons
         q[l] = static_cast<int>(vec2pix_d(kl, M.view[0], M.view[1], M.view[2]));
         omq[l] = 4.0 * kPi / (12 << (2 * kl));
     }
-    double SB[NL], P[NL], Tf[NL], g[NL], SBs[NL];
+    double SB[NL], P[NL], Tf[NL], g[NL], SBs[NL], SBg[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         SB[l] = 0.0;
         SBs[l] = 0.0;
+        SBg[l] = 0.0;
         P[l] = 0.0;
         Tf[l] = 1.0;
         g[l] = VJP ? static_cast<double>(M.dmap[l * npix + pix]) : 0.0;
@@ -283,6 +286,12 @@ __global__ void __launch_bounds__(128) external_map_kernel(const DevGrid G, cons
                 if (pass == 0) {
                     SB[l] += contrib;
                     if (VJP && eta > 0.0) SBs[l] += contrib * (eta_s / eta);  // E is linear in eta
+                    if (VJP && M.dg) {
+                        double E1, dE1;
+                        cell_emission(1.0, kr, ds, &E1, &dE1);
+                        SBg[l] += Tf[l] * E1 * static_cast<double>(__ldg(&M.dg[static_cast<long long>(leaf) * NL + l])) /
+                                  (omq[l] * V);
+                    }
                 } else {
                     P[l] += contrib;
                     const double dSB = Tf[l] * dE - ds * (SB[l] - P[l]);
@@ -308,8 +317,10 @@ __global__ void __launch_bounds__(128) external_map_kernel(const DevGrid G, cons
             for (int l = 0; l < NL; ++l) M.map[l * npix + pix] = static_cast<float>(SB[l]);
         if (pass == 0 && VJP && M.grad_sca)
 #pragma unroll
-            for (int l = 0; l < NL; ++l)
+            for (int l = 0; l < NL; ++l) {
                 if (g[l] * SBs[l] != 0.0) atomicAdd(&M.grad_sca[l], g[l] * SBs[l]);
+                if (M.grad_g && g[l] * SBg[l] != 0.0) atomicAdd(&M.grad_g[l], g[l] * SBg[l]);
+            }
 #pragma unroll
         for (int l = 0; l < NL; ++l) Tf[l] = 1.0;
     }

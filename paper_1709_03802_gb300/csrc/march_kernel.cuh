@@ -58,6 +58,10 @@ struct MarchArgs {
     // batched grids: ledger per model, [model][slot][nl]
     double *mled;
     unsigned long long *mled_fix;
+    // optional tally of d j_sca / d g for one view pixel per wavelength
+    // ([n_leaf][nl]; null: off) and those pixels' directions ([nl])
+    float *dg;
+    const float4 *dg_dir;
 };
 
 // beam solid angle 4 pi / (12 4^k), scaled exactly from float(pi/3)
@@ -649,12 +653,32 @@ __global__ void __launch_bounds__(kMarchBlock, NL == 1 ? kMarchMinBlocks1 : (NL 
                     c_jpix += (lane == j) ? static_cast<unsigned>(npx[l]) : 0u;
                     const long long row0 = G.off_lam[l] + static_cast<long long>(lj) * npx[l];
                     const int ej = det ? cell_exp_jsca(A.eJ[l], __shfl_sync(kFull, kr[l], j), Lj) : 0;
+                    float zs = 0.f, zg = 0.f;  // row sum and its d/dg (tally only)
                     for (int q = lane; q < npx[l]; q += kWarp) {
                         const float4 pd = sh_pix[pixbase[l] + q];
-                        const float r = hg_rsqrt(hgB[l] - hgC[l] * (pd.x * nx + pd.y * ny + pd.z * nz));
+                        const float mu = pd.x * nx + pd.y * ny + pd.z * nz;
+                        const float r = hg_rsqrt(hgB[l] - hgC[l] * mu);
                         const float v = coef * (r * r * r);
                         if (det) atomicAdd(A.pend_fix + row0 + q, to_fix(v, ej));
                         else atomicAdd(A.pend_dst + row0 + q, v);
+                        if (A.dg) {
+                            zs += r * r * r;
+                            zg += 3.f * (mu - 0.5f * hgC[l]) * (r * r * r * r * r);
+                        }
+                    }
+                    if (A.dg) {  // uniform over the warp
+                        for (int o = 16; o > 0; o >>= 1) {
+                            zs += __shfl_xor_sync(kFull, zs, o);
+                            zg += __shfl_xor_sync(kFull, zg, o);
+                        }
+                        if (lane == j) {
+                            const float4 pv = __ldg(&A.dg_dir[l]);
+                            const float mu = pv.x * nx + pv.y * ny + pv.z * nz;
+                            const float r = hg_rsqrt(hgB[l] - hgC[l] * mu);
+                            const float r3 = r * r * r;
+                            atomicAdd(&A.dg[static_cast<long long>(lj) * NL + l],
+                                      coef * (3.f * (mu - 0.5f * hgC[l]) * r3 * r * r - r3 * zg / zs));
+                        }
                     }
                 }
             }

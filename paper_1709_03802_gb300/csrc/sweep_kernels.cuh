@@ -487,6 +487,59 @@ __global__ void rec_scatter_kernel(const PipeDev *pd, const unsigned long long *
     }
 }
 
+// d j_sca / d g tally (gradient of maps with respect to g, the deposited
+// luminosities held fixed): for every buffered record (cell c, ray direction
+// n, coefficient a = L_sca / Z with Z = sum_q t_q^(-3/2), t_q = 1 + g^2 -
+// 2g n_q.n) and the view pixel v of each wavelength,
+//   dg[c] += a (3 (mu_v - g) t_v^(-5/2) - t_v^(-3/2) Z' / Z),
+// Z' = sum_q 3 (mu_q - g) t_q^(-5/2): the derivative of L_sca t_v^(-3/2) / Z.
+// One warp per record, the row sums over the warp's lanes.
+__global__ void dg_tally_kernel(const DevGrid G, const PipeDev *pd, const unsigned long long *rec_n,
+                                const unsigned *cell, const float4 *dir, const float *coef, long long cap,
+                                const float4 *dg_dir, float *dg) {
+    if (!pd->flush) return;
+    const long long n = static_cast<long long>(min(*rec_n, static_cast<unsigned long long>(cap)));
+    const int lane = threadIdx.x & 31;
+    const long long warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+    for (long long i = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5; i < n; i += warps) {
+        const unsigned c = cell[i];
+        if (c == 0xffffffffu) continue;  // a hole
+        const float4 dv = dir[i];
+        for (int l = 0; l < G.nl; ++l) {
+            const float a = G.nl == 1 ? dv.w : coef[l * cap + i];
+            if (a == 0.f) continue;
+            const int k = G.k_lam[l], np = 12 << (2 * k);
+            const float g = G.g[l], B = 1.f + g * g, Cg = 2.f * g;
+            float zs = 0.f, zg = 0.f;
+            for (int q = lane; q < np; q += kWarp) {
+                const float4 p = __ldg(&G.dirtab[dir_tab_offset(k) + q]);
+                const float mu = p.x * dv.x + p.y * dv.y + p.z * dv.z;
+                const float r = hg_rsqrt(B - Cg * mu), r3 = r * r * r;
+                zs += r3;
+                zg += 3.f * (mu - g) * r3 * r * r;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                zs += __shfl_xor_sync(kFull, zs, o);
+                zg += __shfl_xor_sync(kFull, zg, o);
+            }
+            if (lane == 0) {
+                const float4 v = __ldg(&dg_dir[l]);
+                const float mu = v.x * dv.x + v.y * dv.y + v.z * dv.z;
+                const float r = hg_rsqrt(B - Cg * mu), r3 = r * r * r;
+                atomicAdd(&dg[static_cast<long long>(c) * G.nl + l], a * (3.f * (mu - g) * r3 * r * r - r3 * zg / zs));
+            }
+        }
+    }
+}
+
+// The view pixel's direction per wavelength for the d j_sca / d g tally.
+__global__ void dg_dir_kernel(const DevGrid G, double vx, double vy, double vz, float4 *out) {
+    const int l = threadIdx.x;
+    if (l >= G.nl) return;
+    const int k = G.k_lam[l];
+    out[l] = G.dirtab[dir_tab_offset(k) + static_cast<int>(vec2pix_d(k, vx, vy, vz))];
+}
+
 constexpr int kAccRange = 2048;  // records per warp work unit
 
 // Packed single-precision pairs (sm_100+ f32x2): two IEEE fp32 operations per
@@ -843,19 +896,32 @@ __global__ void det_sum_kernel(const float *x, long long n, long long stride, do
     if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
 }
 
-// Deterministic sums of segments: one block per segment (fixed order).
-__global__ void segment_sum_kernel(const float *x, const long long *beg, const long long *len, double *out) {
+// Deterministic sums of segments in two passes with a fixed partition: block
+// (seg, part) sums part `part` of `parts` equal chunks of segment seg, then
+// one thread per segment adds the parts in order.
+__global__ void segment_partial_kernel(const float *x, const long long *beg, const long long *len, int parts,
+                                       double *partial) {
     __shared__ double sh[kBlock];
-    const long long b = beg[blockIdx.x], n = len[blockIdx.x];
+    const int seg = blockIdx.x, part = blockIdx.y;
+    const long long n = len[seg], chunk = (n + parts - 1) / parts;
+    const long long lo = beg[seg] + part * chunk, hi = beg[seg] + min(n, (part + 1) * chunk);
     double s = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += static_cast<double>(x[b + i]);
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += static_cast<double>(x[i]);
     sh[threadIdx.x] = s;
     __syncthreads();
     for (int o = kBlock / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+    if (threadIdx.x == 0) partial[static_cast<long long>(seg) * parts + part] = sh[0];
+}
+
+__global__ void segment_finish_kernel(const double *partial, int nseg, int parts, double *out) {
+    const int seg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (seg >= nseg) return;
+    double s = 0.0;
+    for (int p = 0; p < parts; ++p) s += partial[static_cast<long long>(seg) * parts + p];
+    out[seg] = s;
 }
 
 // j_sca_total += pending, in place.

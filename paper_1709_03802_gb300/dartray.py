@@ -112,9 +112,11 @@ def load(build_if_missing=True):
         "dartray_set_emissivity": ([P, P, C.c_int], C.c_int),
         "dartray_direct_incremental": ([P, P], C.c_int),
         "dartray_map_external": ([P, P, P, P, C.c_double, C.c_int32, C.c_int32, C.c_int32, P, C.c_int], C.c_int),
-        "dartray_map_external_vjp": ([P, P, P, P, C.c_double, C.c_int32, C.c_int32, C.c_int32, P, P, P, C.c_int],
+        "dartray_map_external_vjp": ([P, P, P, P, C.c_double, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, C.c_int],
                                      C.c_int),
         "dartray_set_kappa_rho": ([P, P, C.c_int], C.c_int),
+        "dartray_jsca_dg_arm": ([P, P], C.c_int),
+        "dartray_jsca_dg": ([P, P, C.c_int], C.c_int),
         "dartray_state_load": ([P, C.c_char_p], C.c_int),
         "dartray_grid_destroy": ([P], None),
         "dartray_last_error": ([], C.c_char_p),
@@ -132,7 +134,8 @@ EXPORTED = ("dartray_params_default", "dartray_grid_create", "dartray_direct", "
             "dartray_state_save", "dartray_state_load", "dartray_grid_destroy", "dartray_last_error",
             "dartray_grid_create_batch", "dartray_model_info", "dartray_model_stats", "dartray_autotune",
             "dartray_dust_emission", "dartray_set_emissivity", "dartray_direct_incremental",
-            "dartray_map_external", "dartray_map_external_vjp", "dartray_set_kappa_rho")
+            "dartray_map_external", "dartray_map_external_vjp", "dartray_set_kappa_rho",
+            "dartray_jsca_dg_arm", "dartray_jsca_dg")
 
 
 def _check(rc):
@@ -385,10 +388,12 @@ class DartRay:
                                            _ptr(out), int(_is_cuda_tensor(out))))
         return out
 
-    def map_external_vjp(self, view, up, origin, pixel, nx, ny, dmap, use_jsca=True, out=None, with_albedo=False):
+    def map_external_vjp(self, view, up, origin, pixel, nx, ny, dmap, use_jsca=True, out=None, with_albedo=False,
+                         with_g=False):
         """d/d kappa_rho of sum(dmap * map) (dartray_map_external_vjp):
         [n_leaf][n_lambda]; dmap and out both host arrays or both CUDA
-        tensors.  with_albedo: also return d/d albedo [n_lambda] (float64)."""
+        tensors.  with_albedo / with_g: also return d/d albedo and d/d g
+        [n_lambda] (float64; with_g needs dg_arm(view) before direct())."""
         dev = _is_cuda_tensor(dmap)
         if dev:
             dmap = dmap.contiguous()
@@ -401,9 +406,26 @@ class DartRay:
                 out = np.empty((self.n_leaf, self.n_lambda), np.float32)
         v, u, o = self._frame(view, up, origin)
         ga = np.zeros(self.n_lambda, np.float64)
+        gg = np.zeros(self.n_lambda, np.float64)
         _check(load().dartray_map_external_vjp(self._h, v, u, o, float(pixel), int(nx), int(ny), int(bool(use_jsca)),
-                                               _ptr(dmap), _ptr(out), _ptr(ga), int(dev)))
-        return (out, ga) if with_albedo else out
+                                               _ptr(dmap), _ptr(out), _ptr(ga), _ptr(gg) if with_g else None,
+                                               int(dev)))
+        extra = ((ga,) if with_albedo else ()) + ((gg,) if with_g else ())
+        return (out,) + extra if extra else out
+
+    def dg_arm(self, view):
+        """Arm the tally of d j_sca / d g for the j_sca pixel holding `view`
+        (dartray_jsca_dg_arm); None disarms it.  Takes effect from the next
+        direct()."""
+        v = None if view is None else (C.c_double * 3)(*map(float, view))
+        _check(load().dartray_jsca_dg_arm(self._h, v))
+
+    def dg(self, out=None):
+        """The armed tally [n_leaf][n_lambda] (dartray_jsca_dg)."""
+        if out is None:
+            out = np.empty((self.n_leaf, self.n_lambda), np.float32)
+        _check(load().dartray_jsca_dg(self._h, _ptr(out), int(_is_cuda_tensor(out))))
+        return out
 
     def set_kappa_rho(self, kr):
         k = kr.contiguous() if _is_cuda_tensor(kr) else np.ascontiguousarray(kr, np.float32)
@@ -514,27 +536,49 @@ def dust_self_heating(stellar, dust, lam_ir, dlam_ir, dlam_stellar, scale, f_l=0
     return T, j, hist
 
 
-def external_map(model, kappa_rho, view, up, origin, pixel, nx, ny, use_jsca=True):
+def external_map(model, kappa_rho, view, up, origin, pixel, nx, ny, use_jsca=True, albedo=None, g=None):
     """Differentiable orthographic map: kappa_rho (CUDA tensor [n_leaf][n_lambda])
-    -> map [n_lambda][ny][nx] of `model` (a DartRay), the source (emissivity and
-    j_sca of the last sweep) held fixed.  Forward and backward are the
-    library's map kernel and its reverse march."""
+    -> map [n_lambda][ny][nx] of `model` (a DartRay), the radiation field of
+    the last sweep held fixed.  Forward and backward are the library's map
+    kernel and its reverse march.
+
+    albedo, g: optional tensors [n_lambda] equal to the model's albedo and g;
+    passing them (with requires_grad) gives their gradients too -- the map is
+    differentiated at those values (for g, model.dg_arm(view) must precede
+    the sweep)."""
     import torch
+
+    def same(t, ref, name):
+        if t is not None and not np.allclose(t.detach().cpu().numpy(), np.asarray(ref, np.float64), rtol=1e-6, atol=0):
+            raise ValueError(f"{name} must hold the model's values (the map is differentiated there)")
+
+    same(albedo, model.grid.albedo, "albedo")
+    same(g, model.grid.g, "g")
 
     class _ExternalMap(torch.autograd.Function):
         @staticmethod
-        def forward(ctx, kr):
+        def forward(ctx, kr, alb, gg):
             kr = kr.detach().contiguous()
             model.set_kappa_rho(kr)
             out = torch.empty((model.n_lambda, ny, nx), dtype=torch.float32, device=kr.device)
             model.map_external(view, up, origin, pixel, nx, ny, use_jsca, out=out)
             ctx.save_for_backward(kr)
+            ctx.want = (alb is not None, gg is not None)
             return out
 
         @staticmethod
-        def backward(ctx, g):
+        def backward(ctx, gout):
             (kr,) = ctx.saved_tensors
             model.set_kappa_rho(kr)  # the medium the forward map saw
-            return model.map_external_vjp(view, up, origin, pixel, nx, ny, g.float().contiguous(), use_jsca)
+            wa, wg = ctx.want
+            res = model.map_external_vjp(view, up, origin, pixel, nx, ny, gout.float().contiguous(), use_jsca,
+                                         with_albedo=wa, with_g=wg)
+            if not (wa or wg):
+                return res, None, None
+            res = list(res)
+            gk = res.pop(0)
+            ga = torch.tensor(res.pop(0), dtype=torch.float32, device=kr.device) if wa else None
+            gg = torch.tensor(res.pop(0), dtype=torch.float32, device=kr.device) if wg else None
+            return gk, ga, gg
 
-    return _ExternalMap.apply(kappa_rho)
+    return _ExternalMap.apply(kappa_rho, albedo, g)

@@ -106,3 +106,60 @@ def test_albedo_gradient_matches_direct_light_sweeps():
     fd = ((dmap * mp.map()).sum() - (dmap * mm.map()).sum()) / (float(mp.g.albedo[0]) - float(mm.g.albedo[0]))
     assert abs(ga[0] - fd) <= 1e-8 * abs(fd)
     assert np.count_nonzero(m.eta_sca) > 0
+
+
+def _g_sweep(gval, lib_path=None, view=(0.3, -0.8, 0.52)):
+    g = synth.lognormal_cube(8, 8, tau_mean=2.0, n_src=4)
+    g.g[:] = gval
+    o = oracle.Oracle(g, oracle.OracleParams(a_rt=0.05, r_pre=0.5), lib_path=lib_path)
+    o.dg_arm(view)
+    o.direct()
+    return o
+
+
+def g_tally_pin(lib_path=None):
+    """After step 2 alone the deposited luminosities do not depend on g
+    (nothing scattered has been traced yet), so central differences of the
+    total j_sca pixel holding the view over sweeps at g +- eps give the
+    tally of d j_sca / d g, cell by cell."""
+    view = np.array([0.3, -0.8, 0.52])
+    g0, eps = 0.6, 1e-3
+    o = _g_sweep(g0, lib_path)
+    op, om = _g_sweep(g0 + eps, lib_path), _g_sweep(g0 - eps, lib_path)
+    assert op.k_lam == o.k_lam == om.k_lam  # the same j_sca level (Eq. 5)
+    q = oracle.oracle.vec2pix(o.k_lam[0], view / np.linalg.norm(view))
+    h = float(op.grid.g[0]) - float(om.grid.g[0])  # the step as stored (float32)
+    fd = (op.jsca(0, "total")[:, q] - om.jsca(0, "total")[:, q]) / h
+    dg = o.dg()[:, 0]
+    assert np.count_nonzero(dg) > 0.3 * dg.size
+    assert np.all(np.abs(dg - fd) <= 1e-5 * np.abs(fd).max() + 1e-4 * np.abs(fd))
+    return o, op, om, h
+
+
+def test_g_tally_matches_central_differences():
+    g_tally_pin()
+
+
+def test_g_gradient_of_the_map():
+    o, op, om, h = g_tally_pin()
+    frame = ((0.3, -0.8, 0.52), (0.0, 0.0, 1.0), (-1.6, -1.6), 0.2, 16, 16)
+    m = oracle.ExternalMapOracle(o, *frame)
+    dmap = np.random.default_rng(9).standard_normal((1, 16, 16))
+    gg = m.vjp_g(dmap, o.dg())
+    fd = ((dmap * oracle.ExternalMapOracle(op, *frame).map()).sum() -
+          (dmap * oracle.ExternalMapOracle(om, *frame).map()).sum()) / h
+    assert abs(gg[0] - fd) <= 1e-4 * abs(fd)
+
+
+@pytest.mark.parametrize("name", ["normalisation_dropped", "sign_of_mu"])
+def test_planted_g_tally_mistakes_fail(tmp_path, name):
+    repl = {
+        # the derivative of the normalisation Z left out
+        "normalisation_dropped": [("sca * (or_hg_dg(G->g[l], mu) - or_hg(G->g[l], mu) * Zg[l] / Z[l]) / Z[l];",
+                                   "sca * or_hg_dg(G->g[l], mu) / Z[l];")],
+        # dx/dg taken as 2g + 2mu
+        "sign_of_mu": [("1.5 * (1.0 - g * g) * (2.0 * g - 2.0 * mu)", "1.5 * (1.0 - g * g) * (2.0 * g + 2.0 * mu)")],
+    }[name]
+    path = oracle.build_variant(repl, str(tmp_path))
+    with pytest.raises(AssertionError):
+        g_tally_pin(lib_path=path)
