@@ -66,8 +66,8 @@ RECORD_BYTES = 20
 # of the 1/30000-source case and divided by that case's crossings (ncu:
 # profiles/march_kernel_traffic_galaxy3e5_subset30000.md); a full-size
 # launch's traffic is taken as these times its crossings.
-MARCH_DRAM_BYTES_PER_CROSSING = None
-MARCH_L2_BYTES_PER_CROSSING = None
+MARCH_DRAM_BYTES_PER_CROSSING = 8.24
+MARCH_L2_BYTES_PER_CROSSING = 181.4
 
 
 def l2_copy_gbs():

@@ -30,6 +30,8 @@ def build(force=False, verbose=False):
             return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     flags = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
+    # extra compiler flags, e.g. -DDARTRAY_MARCH_MIN_BLOCKS=6 (tuning builds)
+    flags += os.environ.get("DARTRAY_NVCC_FLAGS", "").split()
     if verbose:
         flags.append("-Xptxas=-v")
     # translation units in parallel, then one link

@@ -11,7 +11,10 @@ enum { MODE_LL = 0, MODE_DIRECT = 1, MODE_SCATTER = 2 };
 constexpr int kBlock = 256;
 // marcher blocks: 128 threads, 5 per SM with one wavelength (96 registers)
 constexpr int kMarchBlock = 128;
-constexpr int kMarchMinBlocks1 = 5;
+#ifndef DARTRAY_MARCH_MIN_BLOCKS
+#define DARTRAY_MARCH_MIN_BLOCKS 5
+#endif
+constexpr int kMarchMinBlocks1 = DARTRAY_MARCH_MIN_BLOCKS;  // resident blocks per SM, one wavelength
 constexpr int kPixTab = 1020;  // pixel centres of levels 0..3 (j_sca levels)
 
 struct MarchArgs {

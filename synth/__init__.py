@@ -9,7 +9,9 @@ float32 so that the float32 GPU path and the float64 oracle see bit-identical
 inputs.
 """
 from .grids import (Grid, lattice_grid, refine_tree, sphere_cube, galaxy_disk,
-                    lognormal_cube, config1, config2, small_sphere)
+                    lognormal_cube, config1, config2, small_sphere, galaxy_particles, particle_galaxy,
+                    config5)
 
 __all__ = ["Grid", "lattice_grid", "refine_tree", "sphere_cube", "galaxy_disk",
-           "lognormal_cube", "config1", "config2", "small_sphere"]
+           "lognormal_cube", "config1", "config2", "small_sphere",
+           "galaxy_particles", "particle_galaxy", "config5"]

@@ -276,3 +276,125 @@ def lognormal_cube(n, seed_index, tau_mean=2.0, sigma_ln=1.0, smooth_cells=2.0, 
     emis = np.zeros(rho_leaf.size)
     emis[src] = 1.0 / (n_src * 4 * math.pi * V)
     return _assemble(topo, kr[:, None], emis[:, None], [albedo], [g], name or f"lognormal{n}")
+
+
+# --------------------------------------------------------------------------- particle galaxy
+def spiral_factor(x, y, amplitude=0.3, pitch_deg=15.0):
+    """Two-arm logarithmic spiral modulation 1 + A cos(2 (phi - ln R / tan(pitch)))."""
+    R = np.maximum(np.sqrt(x * x + y * y), 1e-6)
+    phi = np.arctan2(y, x)
+    return 1.0 + amplitude * np.cos(2.0 * (phi - np.log(R) / math.tan(math.radians(pitch_deg))))
+
+
+def galaxy_particles(n, seed_index=5, h_s=3.0, z_s=0.3, r_e=1.0, bt=0.3, r_max=18.0, z_max=2.0,
+                     amplitude=0.3):
+    """n star particles: an exponential disk (h_s, z_s) with the two-arm
+    spiral modulation (by rejection) and a Sersic n=4 bulge (r_e) holding
+    the fraction bt, within |x|, |y| < r_max and |z| < z_max (kpc)."""
+    rng = np.random.default_rng(SEED_BASE + seed_index)
+    nb = int(round(bt * n))
+    nd = n - nb
+    out = []
+    # disk: R from the Gamma(2, h_s) radial law of an exponential surface density
+    got = 0
+    while got < nd:
+        m = 2 * (nd - got) + 1024
+        R = rng.gamma(2.0, h_s, m)
+        phi = rng.uniform(-math.pi, math.pi, m)
+        z = rng.laplace(0.0, z_s, m)
+        x, y = R * np.cos(phi), R * np.sin(phi)
+        keep = rng.uniform(0.0, 1.0 + amplitude, m) < spiral_factor(x, y, amplitude)
+        keep &= (np.abs(x) < r_max) & (np.abs(y) < r_max) & (np.abs(z) < z_max)
+        p = np.stack([x[keep], y[keep], z[keep]], 1)[: nd - got]
+        out.append(p)
+        got += p.shape[0]
+    # bulge: r by inverting the enclosed-light curve of exp(-7.669 (r/r_e)^(1/4)) on a grid
+    rr = np.geomspace(1e-4, r_max, 4096)
+    dens = np.exp(-7.669 * (rr / r_e) ** 0.25) * rr ** 2
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (dens[1:] + dens[:-1]) * np.diff(rr))])
+    cdf /= cdf[-1]
+    got = 0
+    while got < nb:
+        m = 2 * (nb - got) + 1024
+        r = np.interp(rng.uniform(0.0, 1.0, m), cdf, rr)
+        u = rng.normal(size=(m, 3))
+        p = u / np.linalg.norm(u, axis=1)[:, None] * r[:, None]
+        keep = (np.abs(p[:, 0]) < r_max) & (np.abs(p[:, 1]) < r_max) & (np.abs(p[:, 2]) < z_max)
+        p = p[keep][: nb - got]
+        out.append(p)
+        got += p.shape[0]
+    return np.concatenate(out)
+
+
+def particle_galaxy(n_particles=4_000_000, max_per_leaf=2, max_level=10, tau_b=2.0, h_d=4.5, z_d=0.2,
+                    threshold=0.1, nroot=(9, 9, 1), root_size=4.0, lambdas_um=None, seed_index=5,
+                    name="particle_galaxy"):
+    """The large SPH-like galaxy: star particles (galaxy_particles) deposited
+    on an adaptive tree of root cubes refined, up to max_level times, where a
+    node holds more than max_per_leaf particles or its dust optical depth
+    (max kappa*rho over the node, spiral crest included, times its side)
+    exceeds threshold.  Dust: tau_b/(2 z_d) exp(-R/h_d - |z|/z_d) times the
+    spiral modulation at the cell centre.  Emissivity: the leaf's particles,
+    of equal luminosity (total 1), per volume and sr.  lambdas_um: the
+    wavelengths, kappa ~ lambda^-1.3 normalised at 0.443 um, albedo 0.7 -> 0.4
+    and g 0.75 -> 0.4 linear in log lambda from the first to the last; default
+    one B-band wavelength with albedo 0.6, g 0.6."""
+    p = galaxy_particles(n_particles, seed_index)
+    root_lo = np.array([-0.5 * nroot[0] * root_size, -0.5 * nroot[1] * root_size, -0.5 * nroot[2] * root_size])
+    k0 = tau_b / (2.0 * z_d)
+    rel = p - root_lo[None, :]
+
+    def refine(lo, size, level):
+        s = float(size[0])  # every node of a level has the same side
+        dims = np.array(nroot, np.int64) << level
+        ip = np.floor(rel / s).astype(np.int64)
+        keys = ip[:, 0] + dims[0] * (ip[:, 1] + dims[1] * ip[:, 2])
+        ukeys, counts = np.unique(keys, return_counts=True)
+        il = np.rint((lo - root_lo[None, :]) / s).astype(np.int64)
+        nkeys = il[:, 0] + dims[0] * (il[:, 1] + dims[1] * il[:, 2])
+        pos = np.clip(np.searchsorted(ukeys, nkeys), 0, max(ukeys.size - 1, 0))
+        cnt = np.where(ukeys[pos] == nkeys, counts[pos], 0)
+        hi = lo + size[:, None]
+        cx, cy, cz = (np.clip(0.0, lo[:, a], hi[:, a]) for a in range(3))
+        kmax = k0 * (1.0 + 0.3) * np.exp(-np.sqrt(cx ** 2 + cy ** 2) / h_d - np.abs(cz) / z_d)
+        return (cnt > max_per_leaf) | (kmax * size > threshold)
+
+    topo = (tuple(nroot), tuple(root_lo), root_size) + refine_tree(nroot, root_lo, root_size, max_level, refine)
+    llo, lsz = topo[5], topo[6]
+    c = llo + 0.5 * lsz[:, None]
+    R = np.sqrt(c[:, 0] ** 2 + c[:, 1] ** 2)
+    kr = k0 * np.exp(-R / h_d - np.abs(c[:, 2]) / z_d) * spiral_factor(c[:, 0], c[:, 1])
+    # particles -> leaves by descent, level by level
+    fc = topo[3]
+    lon = topo[4]
+    dims0 = np.array(nroot, np.int64)
+    ip = np.floor(rel / root_size).astype(np.int64)
+    node = ip[:, 0] + dims0[0] * (ip[:, 1] + dims0[1] * ip[:, 2])
+    s = root_size
+    off = rel - ip * root_size
+    while True:
+        child = fc[node]
+        inner = child >= 0
+        if not inner.any():
+            break
+        s *= 0.5
+        b = (off[inner] >= s).astype(np.int64)
+        node[inner] = child[inner] + b[:, 0] + 2 * b[:, 1] + 4 * b[:, 2]
+        off[inner] -= b * s
+    leaf = lon[node]
+    n_leaf = llo.shape[0]
+    counts = np.bincount(leaf, minlength=n_leaf).astype(np.float64)
+    emis = counts / (n_particles * 4 * math.pi * lsz ** 3)
+    if lambdas_um is None:
+        return _assemble(topo, kr[:, None], emis[:, None], [0.6], [0.6], name)
+    lam = np.asarray(lambdas_um, np.float64)
+    t = np.log(lam / lam[0]) / np.log(lam[-1] / lam[0]) if lam.size > 1 else np.zeros(1)
+    krl = kr[:, None] * (lam[None, :] / 0.443) ** -1.3
+    return _assemble(topo, krl, np.repeat(emis[:, None], lam.size, axis=1), 0.7 - 0.3 * t, 0.75 - 0.35 * t, name)
+
+
+def config5(n_lambda=16, **kw):
+    """The large particle galaxy: 4e6 star particles, an adaptive tree of
+    10 levels, 16 wavelengths log-spaced 0.15-2.2 um."""
+    lam = np.geomspace(0.15, 2.2, n_lambda) if n_lambda > 1 else None
+    return particle_galaxy(lambdas_um=lam, name="galaxy_particles", **kw)

@@ -54,8 +54,9 @@ def test_external_map_and_gradients_match_oracle(tmp_path, view):
         b = m.map()
         a = gpu.map_external(view[0], view[1], org, px, nx, ny, use_jsca=use)
         big = b > 1e-6 * b.max()
-        # the 8 emitting cells alone light few lines of sight; j_sca most
-        assert big.sum() > (0.5 * b.size if use else 10)
+        # the 8 emitting cells alone light few lines of sight; j_sca all that
+        # cross the cube (the oblique image is larger than the cube)
+        assert big.sum() > (0.3 * b.size if use else 10)
         assert np.abs(a[big] / b[big] - 1).max() <= 1e-4, use
         assert np.all(np.abs(a[~big]) <= 2e-6 * b.max())
         dmap = rng.standard_normal(b.shape)
