@@ -175,10 +175,14 @@ int dartray_params_default(dartray_params *p);
  * Validate the description, build the leaf face links (ropes) and upload the
  * grid to the current CUDA device; allocate U, U_LL, the two pending j_sca
  * buffers, the total j_sca and the ray queues.  k_lambda,HP per wavelength
- * follows Eq. 5 (integer part, clamped to [0, k_sca_cap]).  cuda_stream is a
- * cudaStream_t (NULL = default stream).  On success *out owns all device
- * memory until dartray_grid_destroy.  Errors: INVAL (bad tree, non-dyadic
- * coordinates, bad sizes), NOMEM, CUDA.
+ * follows Eq. 5 (integer part, clamped to [0, k_sca_cap]).  Any n_lambda
+ * from 1 to 16: rays carry 1, 2, 4, 8 or 16 wavelengths, a count in between
+ * being padded inside the library with wavelengths of no dust and no
+ * emission (j_sca level 0), which every call hides (arrays in and out have
+ * the caller's n_lambda).  cuda_stream is a cudaStream_t (NULL = default
+ * stream).  On success *out owns all device memory until
+ * dartray_grid_destroy.  Errors: INVAL (bad tree, non-dyadic coordinates,
+ * bad sizes), NOMEM, CUDA.
  */
 int dartray_grid_create(const dartray_grid_desc *desc, const dartray_params *params,
                         void *cuda_stream, dartray_grid **out);
@@ -254,7 +258,8 @@ int dartray_scatter_iter(dartray_grid *grid, double *remaining_frac, dartray_sta
  * [n_leaf][n_lambda] (either may be NULL) go to host or device memory;
  * *max_rel_change receives max |j - j_prev| / j_prev over cells and
  * wavelengths with j_prev > 0 (infinite on the first call).  Iterate until
- * it is below 1% (the paper's criterion).  Errors: INVAL, CUDA.
+ * it is below 1% (the paper's criterion).  Both grids have 1, 2, 4, 8 or 16
+ * wavelengths.  Errors: INVAL, CUDA.
  */
 typedef struct dartray_dust {
     int32_t n_ir;                              /* = n_lambda of the dust grid */

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <memory>
 #include <mutex>
+#include <chrono>
 #include <thread>
 #include <utility>
 #include <cmath>
@@ -105,6 +106,9 @@ struct dartray_grid {
     cudaStream_t stream = nullptr;
     dartray_params P{};
     int nl = 0, n_leaf = 0, n_nodes = 0, n_point = 0;
+    // the caller's wavelength count; nl is it rounded up to a marcher width
+    // (1, 2, 4, 8, 16), the extra wavelengths having no dust and no emission
+    int nlu = 0;
     DevGrid G{};
     HostTopo topo;
     // device arrays
@@ -115,6 +119,7 @@ struct dartray_grid {
     float *d_U = nullptr, *d_ULL = nullptr, *d_pend[2] = {nullptr, nullptr}, *d_jtot = nullptr;
     int cur = 0;  // d_pend[cur]: luminosity to emit; d_pend[1-cur]: deposit target
     long long sca_len = 0;
+    long long sca_len_user = 0;  // the j_sca blocks of the caller's wavelengths
     int k_lam[kMaxLambda] = {0};
     long long off_lam[kMaxLambda] = {0};
     // sources
@@ -223,6 +228,29 @@ int copy_in(T *dst, const T *src, size_t count, bool on_device, cudaStream_t s) 
     CK(cudaMemcpyAsync(dst, src, count * sizeof(T), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     return DARTRAY_OK;
 }
+
+// Per-wavelength arrays: the caller's [rows][nlu] <-> the library's
+// [rows][nl] (extra columns zero).
+int copy_in_cols(float *dst, const float *src, size_t rows, int nlu, int nl, bool on_device, cudaStream_t s) {
+    if (nlu == nl) return copy_in(dst, src, rows * nl, on_device, s);
+    if (rows == 0) return DARTRAY_OK;
+    if (!src) return fail(DARTRAY_E_INVAL, "missing input array");
+    CK(cudaMemsetAsync(dst, 0, rows * nl * sizeof(float), s));
+    CK(cudaMemcpy2DAsync(dst, nl * sizeof(float), src, nlu * sizeof(float), nlu * sizeof(float), rows,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return DARTRAY_OK;
+}
+
+int copy_out_cols(float *dst, const float *src, size_t rows, int nlu, int nl, bool dst_is_device, cudaStream_t s) {
+    if (rows == 0) return DARTRAY_OK;
+    const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (nlu == nl) CK(cudaMemcpyAsync(dst, src, rows * nl * sizeof(float), k, s));
+    else CK(cudaMemcpy2DAsync(dst, nlu * sizeof(float), src, nl * sizeof(float), nlu * sizeof(float), rows, k, s));
+    return DARTRAY_OK;
+}
+
+// the marcher width for n wavelengths
+int padded_lambda(int n) { return n <= 1 ? 1 : (n <= 2 ? 2 : (n <= 4 ? 4 : (n <= 8 ? 8 : 16))); }
 
 template <class T>
 int fetch_host(std::vector<T> &dst, const T *src, size_t count, bool on_device) {
@@ -834,15 +862,19 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res, bool keep_U = false) 
             }
             if (!any) break;
             // the first pipeline whose waves have completed
+            // (a round of waves takes milliseconds: after a short spin the
+            // host sleeps between polls instead of holding a core)
             int i = -1;
-            while (i < 0) {
+            for (int spin = 0; i < 0; ++spin) {
                 for (int j = 0; j < kPipes && i < 0; ++j) {
                     if (!inflight[j]) continue;
                     const cudaError_t q = cudaEventQuery(g->pipe[j].ev);
                     if (q == cudaSuccess) i = j;
                     else if (q != cudaErrorNotReady) return fail(DARTRAY_E_CUDA, cudaGetErrorString(q));
                 }
-                if (i < 0) std::this_thread::yield();
+                if (i >= 0) break;
+                if (spin < 64) std::this_thread::yield();
+                else std::this_thread::sleep_for(std::chrono::microseconds(20));
             }
             Pipe &P = g->pipe[i];
             inflight[i] = false;
@@ -1111,14 +1143,14 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
     dartray_params P;
     if (params) P = *params;
     else dartray_params_default(&P);
-    const int nl = desc->n_lambda;
-    if (nl != 1 && nl != 2 && nl != 4 && nl != 8 && nl != 16)
-        return fail(DARTRAY_E_INVAL, "n_lambda must be 1, 2, 4, 8 or 16");
+    const int nlu = desc->n_lambda;
+    if (nlu < 1 || nlu > 16) return fail(DARTRAY_E_INVAL, "n_lambda must be in [1, 16]");
+    const int nl = padded_lambda(nlu);
     long long tot_leaf = 0, tot_nodes = 0, tot_point = 0;
     for (int m = 0; m < n_models; ++m) {
         const dartray_grid_desc &d = descs[m];
         if (d.n_leaf < 1 || d.n_nodes < 1 || d.n_point < 0) return fail(DARTRAY_E_INVAL, "bad sizes");
-        if (d.n_lambda != nl) return fail(DARTRAY_E_INVAL, "the models of a batch must share n_lambda");
+        if (d.n_lambda != nlu) return fail(DARTRAY_E_INVAL, "the models of a batch must share n_lambda");
         tot_leaf += d.n_leaf;
         tot_nodes += d.n_nodes;
         tot_point += d.n_point;
@@ -1137,25 +1169,28 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
         return fail(DARTRAY_E_INVAL, "a batch holds at most 4096 / (6 n_lambda) models");
     const bool on_dev = desc->inputs_on_device != 0;
     std::vector<float> alb, gg;
-    int rc = fetch_host(alb, desc->albedo, nl, on_dev);
+    int rc = fetch_host(alb, desc->albedo, nlu, on_dev);
     if (rc) return rc;
-    rc = fetch_host(gg, desc->g, nl, on_dev);
+    rc = fetch_host(gg, desc->g, nlu, on_dev);
     if (rc) return rc;
-    for (int l = 0; l < nl; ++l)
+    for (int l = 0; l < nlu; ++l)
         if (!(alb[l] >= 0.f && alb[l] <= 1.f) || !(gg[l] > -1.f && gg[l] < 1.f))
             return fail(DARTRAY_E_INVAL, "albedo must be in [0,1] and g in (-1,1)");
     for (int m = 1; m < n_models; ++m) {
         std::vector<float> a2, g2;
-        if ((rc = fetch_host(a2, descs[m].albedo, nl, descs[m].inputs_on_device != 0)) ||
-            (rc = fetch_host(g2, descs[m].g, nl, descs[m].inputs_on_device != 0)))
+        if ((rc = fetch_host(a2, descs[m].albedo, nlu, descs[m].inputs_on_device != 0)) ||
+            (rc = fetch_host(g2, descs[m].g, nlu, descs[m].inputs_on_device != 0)))
             return rc;
         if (a2 != alb || g2 != gg) return fail(DARTRAY_E_INVAL, "the models of a batch must share albedo and g");
     }
+    alb.resize(nl, 0.f);  // the extra wavelengths: no scattering, isotropic
+    gg.resize(nl, 0.f);
 
     dartray_grid *g = new dartray_grid();
     g->P = P;
     g->stream = static_cast<cudaStream_t>(cuda_stream);
     g->nl = nl;
+    g->nlu = nlu;
     g->n_leaf = static_cast<int>(tot_leaf);
     g->n_nodes = static_cast<int>(tot_nodes);
     g->n_point = static_cast<int>(tot_point);
@@ -1253,6 +1288,7 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
         off += tot_leaf * (12ll << (2 * g->k_lam[l]));
     }
     g->sca_len = off;
+    g->sca_len_user = nlu < nl ? g->off_lam[nlu] : off;
 
     const size_t nU = static_cast<size_t>(tot_leaf) * nl;
     const long long ndir = dir_tab_offset(kDirTabLevels + 1);
@@ -1371,10 +1407,10 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
         const dartray_grid_desc &d = descs[m];
         const bool dev_m = d.inputs_on_device != 0;
         const size_t l0 = static_cast<size_t>(g->m_leaf0[m]) * nl, p0 = static_cast<size_t>(g->m_point0[m]);
-        const size_t nUm = static_cast<size_t>(d.n_leaf) * nl;
-        if ((rc = copy_in(g->d_kr + l0, d.kappa_rho, nUm, dev_m, s)) || (rc = copy_in(g->d_emis + l0, d.emissivity, nUm, dev_m, s)) ||
+        if ((rc = copy_in_cols(g->d_kr + l0, d.kappa_rho, d.n_leaf, nlu, nl, dev_m, s)) ||
+            (rc = copy_in_cols(g->d_emis + l0, d.emissivity, d.n_leaf, nlu, nl, dev_m, s)) ||
             (rc = copy_in(g->d_pxyz + 3 * p0, d.point_xyz, 3ull * d.n_point, dev_m, s)) ||
-            (rc = copy_in(g->d_plum + p0 * nl, d.point_lum, static_cast<size_t>(d.n_point) * nl, dev_m, s)))
+            (rc = copy_in_cols(g->d_plum + p0 * nl, d.point_lum, d.n_point, nlu, nl, dev_m, s)))
             return bail(rc);
         leaf_model.insert(leaf_model.end(), d.n_leaf, static_cast<uint16_t>(m));
         point_model.insert(point_model.end(), d.n_point, static_cast<uint16_t>(m));
@@ -1419,6 +1455,7 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
     G.n_nodes = static_cast<int>(tot_nodes);
     G.n_leaf = static_cast<int>(tot_leaf);
     G.nl = nl;
+    G.nl_user = nlu;
     G.n_point = static_cast<int>(tot_point);
     G.n_models = n_models;
     G.models = g->d_models;
@@ -1634,15 +1671,17 @@ int dartray_map_external(dartray_grid *g, const double view[3], const double up[
     int rc = external_frame(g, view, up, origin, pixel, nx, ny, &M);
     if (rc) return rc;
     if ((rc = set_device(g))) return rc;
-    const size_t n = static_cast<size_t>(nx) * ny * g->nl;
+    const size_t n = static_cast<size_t>(nx) * ny * g->nl, n_user = static_cast<size_t>(nx) * ny * g->nlu;
     float *dst = map;
-    if (!dst_is_device && (rc = stage_buffer(g, n, &dst))) return rc;
+    if ((!dst_is_device || g->nlu < g->nl) && (rc = stage_buffer(g, n, &dst))) return rc;
     M.jsca = use_jsca ? g->d_jtot : nullptr;
     M.map = dst;
     if (launch_external_map(g->G, M, false, g->stream)) return fail(DARTRAY_E_INVAL, "unsupported n_lambda");
     ++g->launches;
     CK(cudaGetLastError());
-    if (!dst_is_device) CK(cudaMemcpyAsync(map, dst, n * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    if (dst != map)  // the caller's wavelengths are the first rows
+        CK(cudaMemcpyAsync(map, dst, n_user * sizeof(float),
+                           dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
 }
@@ -1662,18 +1701,24 @@ int dartray_map_external_vjp(dartray_grid *g, const double view[3], const double
     }
     if ((rc = set_device(g))) return rc;
     const size_t n = static_cast<size_t>(nx) * ny * g->nl, nU = static_cast<size_t>(g->n_leaf) * g->nl;
+    const size_t n_user = static_cast<size_t>(nx) * ny * g->nlu;
+    const bool padded = g->nlu < g->nl;
     // the grid's staging buffer holds the per-wavelength sums (two rows of
-    // doubles, at its start) and, for host arguments, the upstream gradient
-    // and the result
+    // doubles, at its start) and, for host arguments or extra wavelengths,
+    // the upstream gradient (zero rows for the extra wavelengths) and the
+    // result
     const size_t n_dbl = 4 * kMaxLambda;  // in floats
+    const bool staged = !on_device || padded;
     float *st = nullptr;
-    if ((rc = stage_buffer(g, n_dbl + (on_device ? 0 : n + nU), &st))) return rc;
+    if ((rc = stage_buffer(g, n_dbl + (staged ? n + nU : 0), &st))) return rc;
     double *d_gs = reinterpret_cast<double *>(st);
     float *d_in = const_cast<float *>(dmap), *d_out = grad_kappa_rho;
-    if (!on_device) {
+    if (staged) {
         d_in = st + n_dbl;
         d_out = st + n_dbl + n;
-        CK(cudaMemcpyAsync(d_in, dmap, n * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+        if (padded) CK(cudaMemsetAsync(d_in + n_user, 0, (n - n_user) * sizeof(float), g->stream));
+        CK(cudaMemcpyAsync(d_in, dmap, n_user * sizeof(float),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
     }
     CK(cudaMemsetAsync(d_out, 0, nU * sizeof(float), g->stream));
     CK(cudaMemsetAsync(d_gs, 0, 2 * kMaxLambda * sizeof(double), g->stream));
@@ -1686,15 +1731,16 @@ int dartray_map_external_vjp(dartray_grid *g, const double view[3], const double
     if (launch_external_map(g->G, M, true, g->stream)) return fail(DARTRAY_E_INVAL, "unsupported n_lambda");
     ++g->launches;
     CK(cudaGetLastError());
-    if (!on_device) CK(cudaMemcpyAsync(grad_kappa_rho, d_out, nU * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    if (staged && (rc = copy_out_cols(grad_kappa_rho, d_out, g->n_leaf, g->nlu, g->nl, on_device != 0, g->stream)))
+        return rc;
     double gs[2 * kMaxLambda];
     CK(cudaMemcpyAsync(gs, d_gs, 2 * kMaxLambda * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     // j_sca is proportional to the albedo (the radiation field held fixed)
     if (grad_albedo)
-        for (int l = 0; l < g->nl; ++l) grad_albedo[l] = g->G.albedo[l] > 0 ? gs[l] / g->G.albedo[l] : 0.0;
+        for (int l = 0; l < g->nlu; ++l) grad_albedo[l] = g->G.albedo[l] > 0 ? gs[l] / g->G.albedo[l] : 0.0;
     if (grad_g)
-        for (int l = 0; l < g->nl; ++l) grad_g[l] = gs[kMaxLambda + l];
+        for (int l = 0; l < g->nlu; ++l) grad_g[l] = gs[kMaxLambda + l];
     return DARTRAY_OK;
 }
 
@@ -1733,9 +1779,7 @@ int dartray_jsca_dg(dartray_grid *g, float *out, int dst_is_device) {
     if (!g->dg_on) return fail(DARTRAY_E_STATE, "the g tally is not armed");
     int rc = set_device(g);
     if (rc) return rc;
-    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
-    CK(cudaMemcpyAsync(out, g->d_dg, nU * sizeof(float), dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       g->stream));
+    if ((rc = copy_out_cols(out, g->d_dg, g->n_leaf, g->nlu, g->nl, dst_is_device != 0, g->stream))) return rc;
     CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
 }
@@ -1745,8 +1789,7 @@ int dartray_set_kappa_rho(dartray_grid *g, const float *kappa_rho, int src_is_de
     if (!g || !kappa_rho) return fail(DARTRAY_E_INVAL, "null argument");
     int rc = set_device(g);
     if (rc) return rc;
-    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
-    if ((rc = copy_in(g->d_kr, kappa_rho, nU, src_is_device != 0, g->stream))) return rc;
+    if ((rc = copy_in_cols(g->d_kr, kappa_rho, g->n_leaf, g->nlu, g->nl, src_is_device != 0, g->stream))) return rc;
     CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
 }
@@ -1756,8 +1799,7 @@ int dartray_set_emissivity(dartray_grid *g, const float *emis, int src_is_device
     if (!g || !emis) return fail(DARTRAY_E_INVAL, "null argument");
     int rc = set_device(g);
     if (rc) return rc;
-    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
-    if ((rc = copy_in(g->d_emis, emis, nU, src_is_device != 0, g->stream))) return rc;
+    if ((rc = copy_in_cols(g->d_emis, emis, g->n_leaf, g->nlu, g->nl, src_is_device != 0, g->stream))) return rc;
     CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
 }
@@ -1795,6 +1837,8 @@ int dartray_dust_emission(dartray_grid *ir, const dartray_grid *stellar, const d
                           float *j, int dst_is_device, double *max_rel_change) {
     g_last_error.clear();
     if (!ir || !stellar || !dust) return fail(DARTRAY_E_INVAL, "null argument");
+    if (ir->nlu != ir->nl || stellar->nlu != stellar->nl)
+        return fail(DARTRAY_E_INVAL, "dust emission: grids of 1, 2, 4, 8 or 16 wavelengths");
     if (ir->n_leaf != stellar->n_leaf || dust->n_ir != ir->nl || dust->n_stellar != stellar->nl ||
         !(dust->scale > 0) || !(dust->t_min > 0) || !(dust->t_max > dust->t_min) || ir->device != stellar->device)
         return fail(DARTRAY_E_INVAL, "dust emission: grids or parameters do not match");
@@ -1906,16 +1950,17 @@ int dartray_rfed(dartray_grid *g, float *U, float *L_abs, int dst_is_device) {
     int rc = set_device(g);
     if (rc) return rc;
     const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
-    const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (U) CK(cudaMemcpyAsync(U, g->d_U, nU * sizeof(float), k, g->stream));
+    const bool padded = g->nlu < g->nl;
+    if (U && (rc = copy_out_cols(U, g->d_U, g->n_leaf, g->nlu, g->nl, dst_is_device != 0, g->stream))) return rc;
     if (L_abs) {
         float *dst = L_abs;
-        if (!dst_is_device && (rc = stage_buffer(g, nU, &dst))) return rc;
+        if ((!dst_is_device || padded) && (rc = stage_buffer(g, nU, &dst))) return rc;
         labs_kernel<<<static_cast<unsigned>((nU + kBlock - 1) / kBlock), kBlock, 0, g->stream>>>(
             g->G, g->d_U, static_cast<float>(g->P.c_light), dst);
         ++g->launches;
         CK(cudaGetLastError());
-        if (!dst_is_device) CK(cudaMemcpyAsync(L_abs, dst, nU * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+        if (dst != L_abs && (rc = copy_out_cols(L_abs, dst, g->n_leaf, g->nlu, g->nl, dst_is_device != 0, g->stream)))
+            return rc;
     }
     CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
@@ -1923,11 +1968,11 @@ int dartray_rfed(dartray_grid *g, float *U, float *L_abs, int dst_is_device) {
 
 int dartray_jsca_layout(const dartray_grid *g, int32_t *k_lambda, int64_t *offsets, int64_t *total_len) {
     if (!g) return fail(DARTRAY_E_INVAL, "null grid");
-    for (int l = 0; l < g->nl; ++l) {
+    for (int l = 0; l < g->nlu; ++l) {
         if (k_lambda) k_lambda[l] = g->k_lam[l];
         if (offsets) offsets[l] = g->off_lam[l];
     }
-    if (total_len) *total_len = g->sca_len;
+    if (total_len) *total_len = g->sca_len_user;
     return DARTRAY_OK;
 }
 
@@ -1937,7 +1982,7 @@ int dartray_jsca(dartray_grid *g, int which, float *out, int dst_is_device) {
     int rc = set_device(g);
     if (rc) return rc;
     const float *src = which == 0 ? g->d_jtot : g->d_pend[1 - g->cur];
-    CK(cudaMemcpyAsync(out, src, g->sca_len * sizeof(float),
+    CK(cudaMemcpyAsync(out, src, g->sca_len_user * sizeof(float),
                        dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
@@ -1952,9 +1997,9 @@ int dartray_map(dartray_grid *g, const double observer[3], int32_t nside_k, int3
     int rc = set_device(g);
     if (rc) return rc;
     const long long npix = 12ll << (2 * nside_k);
-    const size_t nmap = static_cast<size_t>(npix) * g->nl;
+    const size_t nmap = static_cast<size_t>(npix) * g->nl, nmap_user = static_cast<size_t>(npix) * g->nlu;
     float *dst = map;
-    if (!dst_is_device && (rc = stage_buffer(g, nmap, &dst))) return rc;
+    if ((!dst_is_device || g->nlu < g->nl) && (rc = stage_buffer(g, nmap, &dst))) return rc;
     CK(cudaMemsetAsync(dst, 0, nmap * sizeof(float), g->stream));
     MapArgs M{};
     for (int a = 0; a < 3; ++a) M.obs[a] = observer[a];  // double: exact subdivision / pixel decisions
@@ -1967,7 +2012,10 @@ int dartray_map(dartray_grid *g, const double observer[3], int32_t nside_k, int3
     if (rc) return fail(DARTRAY_E_INVAL, "unsupported n_lambda for maps");
     ++g->launches;
     CK(cudaGetLastError());
-    if (!dst_is_device) CK(cudaMemcpyAsync(map, dst, nmap * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    // the caller's wavelengths are the first rows
+    if (dst != map)
+        CK(cudaMemcpyAsync(map, dst, nmap_user * sizeof(float),
+                           dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
 }
@@ -2024,7 +2072,7 @@ int dartray_map_noalloc(dartray_grid *g, const double observer[3], int32_t nside
     if (rc) return fail(DARTRAY_E_INVAL, "unsupported n_lambda for maps");
     ++g->launches;
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(map, scratch, static_cast<size_t>(nmap) * sizeof(float),
+    CK(cudaMemcpyAsync(map, scratch, static_cast<size_t>(npix) * g->nlu * sizeof(float),
                        dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
@@ -2036,19 +2084,24 @@ int dartray_state_save(dartray_grid *g, const char *path) {
     if (g->n_models > 1) return fail(DARTRAY_E_INVAL, "state files hold single-model grids");
     int rc = set_device(g);
     if (rc) return rc;
-    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
-    std::vector<float> buf(std::max<size_t>(nU, g->sca_len));
+    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nlu;
+    std::vector<float> buf(std::max<size_t>(nU, g->sca_len_user));
     FILE *f = std::fopen(path, "wb");
     if (!f) return fail(DARTRAY_E_INVAL, std::string("cannot open ") + path);
     const char magic[8] = {'D', 'R', 'T', 'S', 'T', 'A', 'T', '1'};
-    long long hdr[4] = {g->n_leaf, g->nl, g->sca_len, g->have_direct ? 1 : 0};
+    long long hdr[4] = {g->n_leaf, g->nlu, g->sca_len_user, g->have_direct ? 1 : 0};
     bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof hdr, 1, f) == 1 &&
               std::fwrite(&g->l_sca2, sizeof(double), 1, f) == 1;
     const float *arrs[5] = {g->d_U, g->d_ULL, g->d_pend[g->cur], g->d_pend[1 - g->cur], g->d_jtot};
-    const size_t lens[5] = {nU, nU, static_cast<size_t>(g->sca_len), static_cast<size_t>(g->sca_len),
-                            static_cast<size_t>(g->sca_len)};
+    const size_t lens[5] = {nU, nU, static_cast<size_t>(g->sca_len_user), static_cast<size_t>(g->sca_len_user),
+                            static_cast<size_t>(g->sca_len_user)};
     for (int i = 0; i < 5 && ok; ++i) {
-        if (cudaMemcpy(buf.data(), arrs[i], lens[i] * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        // [n_leaf][nlu] fields and the first nlu j_sca blocks
+        const bool fail_copy = i < 2 ? copy_out_cols(buf.data(), arrs[i], g->n_leaf, g->nlu, g->nl, false, g->stream) != 0 ||
+                                           cudaStreamSynchronize(g->stream) != cudaSuccess
+                                     : cudaMemcpy(buf.data(), arrs[i], lens[i] * sizeof(float), cudaMemcpyDeviceToHost) !=
+                                           cudaSuccess;
+        if (fail_copy) {
             std::fclose(f);
             return fail(DARTRAY_E_CUDA, "copy failed");
         }
@@ -2064,7 +2117,7 @@ int dartray_state_load(dartray_grid *g, const char *path) {
     if (g->n_models > 1) return fail(DARTRAY_E_INVAL, "state files hold single-model grids");
     int rc = set_device(g);
     if (rc) return rc;
-    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nl;
+    const size_t nU = static_cast<size_t>(g->n_leaf) * g->nlu;
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(DARTRAY_E_INVAL, std::string("cannot open ") + path);
     char magic[8];
@@ -2072,19 +2125,28 @@ int dartray_state_load(dartray_grid *g, const char *path) {
     double l2 = 0;
     bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "DRTSTAT1", 8) == 0 &&
               std::fread(hdr, sizeof hdr, 1, f) == 1 && std::fread(&l2, sizeof(double), 1, f) == 1 &&
-              hdr[0] == g->n_leaf && hdr[1] == g->nl && hdr[2] == g->sca_len;
+              hdr[0] == g->n_leaf && hdr[1] == g->nlu && hdr[2] == g->sca_len_user;
     if (!ok) {
         std::fclose(f);
         return fail(DARTRAY_E_INVAL, "state file does not match this grid");
     }
-    std::vector<float> buf(std::max<size_t>(nU, g->sca_len));
+    std::vector<float> buf(std::max<size_t>(nU, g->sca_len_user));
     g->cur = 0;
     float *arrs[5] = {g->d_U, g->d_ULL, g->d_pend[0], g->d_pend[1], g->d_jtot};
-    const size_t lens[5] = {nU, nU, static_cast<size_t>(g->sca_len), static_cast<size_t>(g->sca_len),
-                            static_cast<size_t>(g->sca_len)};
+    const size_t lens[5] = {nU, nU, static_cast<size_t>(g->sca_len_user), static_cast<size_t>(g->sca_len_user),
+                            static_cast<size_t>(g->sca_len_user)};
+    const size_t tail = static_cast<size_t>(g->sca_len - g->sca_len_user);  // blocks of the extra wavelengths
     for (int i = 0; i < 5 && ok; ++i) {
         ok = std::fread(buf.data(), sizeof(float), lens[i], f) == lens[i];
-        if (ok && cudaMemcpy(arrs[i], buf.data(), lens[i] * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+        bool bad = false;
+        if (ok && i < 2) {
+            bad = copy_in_cols(arrs[i], buf.data(), g->n_leaf, g->nlu, g->nl, false, g->stream) != 0 ||
+                  cudaStreamSynchronize(g->stream) != cudaSuccess;
+        } else if (ok) {
+            bad = cudaMemcpy(arrs[i], buf.data(), lens[i] * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+                  (tail && cudaMemset(arrs[i] + g->sca_len_user, 0, tail * sizeof(float)) != cudaSuccess);
+        }
+        if (bad) {
             std::fclose(f);
             return fail(DARTRAY_E_CUDA, "copy failed");
         }

@@ -33,6 +33,7 @@ struct DevGrid {
     float root_lo[3];
     float root_size;
     int n_nodes, n_leaf, nl, n_point;
+    int nl_user;                // the caller's wavelengths: [0, nl_user); the rest pad nl
     const int32_t *node_child;  // first child, or -(leaf+1)
     const float4 *node_box;     // lo.xyz, side
     const float4 *leaf_box;

@@ -99,10 +99,13 @@ def test_rejects_bad_albedo():
     assert rc == -1
 
 
-def test_rejects_unsupported_lambda_count():
+@pytest.mark.parametrize("n", [0, 17])
+def test_rejects_unsupported_lambda_count(n):
+    """1 to 16 wavelengths (counts between the marcher widths 1, 2, 4, 8, 16
+    are padded inside the library)."""
     grid = synth.config1()
     d, keep = _desc(grid)
-    d.n_lambda = 3
+    d.n_lambda = n
     rc, msg = _create(d)
     assert rc == -1 and "n_lambda" in msg
 

@@ -125,6 +125,67 @@ def test_multi_lambda():
     run_pair(grid, 1, a_rt=0.05, r_pre=0.4)
 
 
+def _to_device(grid):
+    """The grid with every input array on the GPU (inputs_on_device)."""
+    import dataclasses
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    return dataclasses.replace(
+        grid, first_child=t(grid.first_child), leaf_of_node=t(grid.leaf_of_node), kappa_rho=t(grid.kappa_rho),
+        emissivity=t(grid.emissivity), albedo=t(grid.albedo), g=t(grid.g),
+        point_xyz=torch.zeros((0, 3), device="cuda"), point_lum=torch.zeros((0, grid.n_lambda), device="cuda"))
+
+
+@pytest.mark.parametrize("nl", [3, 5])
+def test_wavelength_counts_between_marcher_widths(nl, tmp_path):
+    """3 and 5 wavelengths, which the library pads to rays of 4 and 8: the
+    ledger, RFED and j_sca of every wavelength, the internal and the
+    distant-observer maps, device inputs and outputs and the state file,
+    all in the caller's layout, against the oracle."""
+    g1 = synth.small_sphere(7, cell=0.25, radius=0.7, tau_radial=1.0)
+    f = np.array([1.6, 1.0, 0.6, 0.3, 0.2], np.float32)[:nl]
+    kr = g1.kappa_rho * f[None, :]
+    em = np.repeat(g1.emissivity, nl, axis=1) * np.array([0.5, 1.0, 1.0, 0.7, 0.9], np.float32)[None, :nl]
+    grid = g1.with_lambda(kr, em, [0.7, 0.6, 0.5, 0.45, 0.4][:nl], [0.75, 0.6, 0.5, 0.45, 0.3][:nl])
+    gpu, ref = run_pair(grid, 1, a_rt=0.05, r_pre=0.4)
+    assert list(gpu.k_lam) == list(ref.k_lam) and list(gpu.off_lam) == list(ref.off_lam)
+    assert gpu.sca_len == ref.jsca_total.size
+    for l in range(nl):
+        a, b = gpu.jsca_block(l), ref.jsca(l)
+        big = b > 1e-6 * b.max()
+        assert np.abs(a[big] / b[big] - 1).max() <= REL_CELL, l
+    obs = [0.3, -0.2, 0.1]
+    a, b = gpu.map(obs, 3, max_sub=3), ref.map(obs, 3, max_sub=3)
+    assert a.shape == b.shape == (nl, 12 * 4 ** 3)
+    big = b > 1e-6 * b.max()
+    assert np.abs(a[big] / b[big] - 1).max() <= REL_CELL
+    frame = ((0.3, -0.8, 0.52), (0.0, 0.0, 1.0), (-1.4, -1.4), 0.1, 28, 28)
+    e = gpu.map_external(*frame)
+    r = oracle.ExternalMapOracle(ref, *frame).map()
+    big = r > 1e-6 * r.max()
+    assert e.shape == (nl, 28, 28) and np.abs(e[big] / r[big] - 1).max() <= REL_CELL
+    dm = np.random.default_rng(5).standard_normal((nl, 28, 28)).astype(np.float32)
+    gk_host = gpu.map_external_vjp(*frame, dm)
+    gk_dev = gpu.map_external_vjp(*frame, torch.tensor(dm, device="cuda"))
+    assert gk_host.shape == (grid.n_leaf, nl)
+    assert np.allclose(gk_dev.cpu().numpy(), gk_host, rtol=1e-5, atol=1e-6 * np.abs(gk_host).max())
+    U_dev = torch.empty((grid.n_leaf, nl), dtype=torch.float32, device="cuda")
+    gpu.rfed(U=U_dev)
+    U_host, L_host = gpu.rfed()
+    assert np.array_equal(U_dev.cpu().numpy(), U_host)
+    path = str(tmp_path / "state.bin")
+    gpu.save(path)
+    other = DartRay(grid, r_pre=0.4)
+    other.load(path)
+    assert np.array_equal(other.rfed()[0], U_host)
+    assert np.array_equal(other.jsca(), gpu.jsca())
+    on_dev = DartRay(_to_device(grid), r_pre=0.4)
+    on_dev.direct()
+    Ud, _ = on_dev.rfed()
+    st_ref = DartRay(grid, r_pre=0.4)
+    st_ref.direct()
+    assert np.abs(Ud - st_ref.rfed()[0]).max() <= 1e-5 * Ud.max()
+
+
 def test_point_sources():
     g = synth.lognormal_cube(8, 4, n_src=3, tau_mean=1.5)
     pts = np.array([[0.13, -0.27, 0.41], [-0.6, 0.2, -0.05]], np.float32)
