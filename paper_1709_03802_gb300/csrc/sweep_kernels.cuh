@@ -248,7 +248,10 @@ __global__ void model_count_kernel(const DevGrid G, const int *flags, int n, int
 __global__ void threshold_kernel(const DevGrid G, const float *U_LL, const float *f_u_model, float *thr) {
     const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     if (i >= static_cast<long long>(G.n_leaf) * G.nl) return;
-    thr[i] = f_u_model[model_of_leaf(G, static_cast<int>(i / G.nl))] * U_LL[i];
+    // a padding wavelength (no light, no dust) is negligible everywhere, so it
+    // never keeps a ray going (Eq. 1 with an infinite threshold)
+    thr[i] = static_cast<int>(i % G.nl) >= G.nl_user ? __int_as_float(0x7f800000)
+                                                      : f_u_model[model_of_leaf(G, static_cast<int>(i / G.nl))] * U_LL[i];
 }
 
 // Block-level exclusive scan of flags -> per-block totals.
@@ -730,11 +733,182 @@ __device__ inline void accumulate_range(const DevGrid &G, const FlushArgs &F, in
     flush(cur);
 }
 
+// Float mode with records merged first: rays of different sources that reach
+// a cell at the same HEALPix level and pixel carry bitwise-equal directions,
+// and their weight rows differ only by the coefficient, so a cell's records
+// are summed per direction in a per-warp hash table (shared memory) and each
+// distinct direction is expanded once.  Runs of fewer than kMergeMin records
+// of one cell are expanded directly.
+#ifndef DARTRAY_FLUSH_MERGE
+#define DARTRAY_FLUSH_MERGE 1  // 0: expand every record (tuning builds)
+#endif
+constexpr int kMergeSlots = 256;                 // hash slots per warp
+constexpr int kMergeMin = 64;                    // records of a cell worth merging
+constexpr unsigned kEmptySlot = 0xffffffffu;     // x bits of an empty slot (a NaN: no direction)
+
+__device__ __forceinline__ unsigned dir_hash(unsigned x, unsigned y, unsigned z) {
+    unsigned h = x * 0x9E3779B1u ^ (y * 0x85EBCA77u + 0x27D4EB2Fu) ^ (z * 0xC2B2AE3Du + 0x165667B1u);
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    return h ^ (h >> 12);
+}
+
+template <int PPL>
+__device__ inline void accumulate_range_merged(const DevGrid &G, const FlushArgs &F, int l, long long beg,
+                                               long long end, long long total, int lane, ulonglong2 *sh_rec,
+                                               ulonglong2 *sh_rec2, float4 *tab) {
+    constexpr int NP2 = (PPL + 1) / 2;
+    const int k = G.k_lam[l];
+    const int np = 12 << (2 * k);
+    const float B = 1.f + G.g[l] * G.g[l], Cg = 2.f * G.g[l];
+    unsigned long long mx[NP2], my[NP2], mz[NP2], acc[NP2];
+#pragma unroll
+    for (int i = 0; i < NP2; ++i) {
+        const int q0 = lane + kWarp * (2 * i), q1 = lane + kWarp * (2 * i + 1);
+        const float4 a = q0 < np ? __ldg(&G.dirtab[dir_tab_offset(k) + q0]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = q1 < np ? __ldg(&G.dirtab[dir_tab_offset(k) + q1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        mx[i] = f2_pack(make_float2(-a.x, -b.x));
+        my[i] = f2_pack(make_float2(-a.y, -b.y));
+        mz[i] = f2_pack(make_float2(-a.z, -b.z));
+        acc[i] = f2_pack(make_float2(0.f, 0.f));
+    }
+    const unsigned long long B2 = f2_pack(make_float2(B, B));
+    const unsigned below = (1u << lane) - 1u;
+    auto stage = [&](int pos, float x, float y, float z, float cf) {
+        sh_rec[pos] = make_ulonglong2(f2_pack(make_float2(Cg * x, Cg * x)), f2_pack(make_float2(Cg * y, Cg * y)));
+        sh_rec2[pos] = make_ulonglong2(f2_pack(make_float2(Cg * z, Cg * z)), f2_pack(make_float2(cf, cf)));
+    };
+    // the weights of cnt staged records (one cell) into acc, two at a time
+    auto expand = [&](int cnt) {
+        int j = 0;
+        while (j < cnt) {
+            const ulonglong2 ra = sh_rec[j], rb = sh_rec2[j];
+            const unsigned long long cx = ra.x, cy = ra.y, cz = rb.x, cc = rb.y;
+            if (j + 1 < cnt) {
+                const ulonglong2 ra1 = sh_rec[j + 1], rb1 = sh_rec2[j + 1];
+                const unsigned long long dx = ra1.x, dy = ra1.y, dz = rb1.x, dc = rb1.y;
+#pragma unroll
+                for (int i = 0; i < NP2; ++i) {
+                    unsigned long long t = f2_fma(mx[i], cx, B2), u = f2_fma(mx[i], dx, B2);
+                    t = f2_fma(my[i], cy, t);
+                    u = f2_fma(my[i], dy, u);
+                    t = f2_fma(mz[i], cz, t);
+                    u = f2_fma(mz[i], dz, u);
+                    const float2 tv = f2_unpack(t), uv = f2_unpack(u);
+                    const unsigned long long rt = f2_pack(make_float2(hg_rsqrt(tv.x), hg_rsqrt(tv.y)));
+                    const unsigned long long ru = f2_pack(make_float2(hg_rsqrt(uv.x), hg_rsqrt(uv.y)));
+                    const unsigned long long wt = f2_mul(f2_mul(rt, rt), rt), wu = f2_mul(f2_mul(ru, ru), ru);
+                    acc[i] = f2_fma(dc, wu, f2_fma(cc, wt, acc[i]));
+                }
+                j += 2;
+            } else {
+#pragma unroll
+                for (int i = 0; i < NP2; ++i) {
+                    unsigned long long t = f2_fma(mx[i], cx, B2);
+                    t = f2_fma(my[i], cy, t);
+                    t = f2_fma(mz[i], cz, t);
+                    const float2 tv = f2_unpack(t);
+                    const unsigned long long rr = f2_pack(make_float2(hg_rsqrt(tv.x), hg_rsqrt(tv.y)));
+                    acc[i] = f2_fma(cc, f2_mul(f2_mul(rr, rr), rr), acc[i]);
+                }
+                j += 1;
+            }
+        }
+    };
+    auto flush = [&](int c) {
+        const long long row = G.off_lam[l] + static_cast<long long>(c) * np;
+#pragma unroll
+        for (int i = 0; i < NP2; ++i) {
+            const int q0 = lane + kWarp * (2 * i), q1 = lane + kWarp * (2 * i + 1);
+            const float2 v = f2_unpack(acc[i]);
+            if (q0 < np && v.x != 0.f) atomicAdd(F.pend + row + q0, v.x);
+            if (q1 < np && v.y != 0.f) atomicAdd(F.pend + row + q1, v.y);
+            acc[i] = f2_pack(make_float2(0.f, 0.f));
+        }
+    };
+    for (int i = lane; i < kMergeSlots; i += kWarp) tab[i] = make_float4(__uint_as_float(kEmptySlot), 0.f, 0.f, 0.f);
+    __syncwarp();
+    int used = 0;  // occupied slots (warp-uniform)
+    // expand every occupied slot and empty the table
+    auto drain = [&]() {
+        for (int base = 0; base < kMergeSlots; base += kWarp) {
+            const float4 e = tab[base + lane];
+            const bool occ = __float_as_uint(e.x) != kEmptySlot;
+            const unsigned m = __ballot_sync(kFull, occ);
+            if (occ) stage(__popc(m & below), e.x, e.y, e.z, e.w);
+            __syncwarp();
+            expand(__popc(m));
+            __syncwarp();
+            tab[base + lane] = make_float4(__uint_as_float(kEmptySlot), 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        used = 0;
+    };
+    int cur = cell_of_record(F.off, F.n_leaf, beg, lane);
+    long long p = beg;
+    while (p < end) {
+        const long long nb = cur + 1 < F.n_leaf ? static_cast<long long>(F.off[cur + 1]) : total;
+        const long long e = min(end, nb);  // cur's records in this range: [p, e)
+        const bool merge = e - p >= kMergeMin;
+        for (long long b = p; b < e; b += kWarp) {
+            const long long r = b + lane;
+            const bool have = r < e;
+            const float4 dv = have ? F.sdir[r] : make_float4(__uint_as_float(kEmptySlot), 0.f, 0.f, 0.f);
+            const float cf = have ? (F.packed ? dv.w : F.scoef[l * F.cap + r]) : 0.f;
+            if (!merge) {
+                if (have) stage(lane, dv.x, dv.y, dv.z, cf);
+                __syncwarp();
+                expand(static_cast<int>(min(static_cast<long long>(kWarp), e - b)));
+                __syncwarp();
+                continue;
+            }
+            if (used > kMergeSlots / 2) drain();  // at most 5/8 full after this chunk: probes end
+            const unsigned kx = __float_as_uint(dv.x), ky = __float_as_uint(dv.y), kz = __float_as_uint(dv.z);
+            // lanes holding the same direction: the lowest inserts, all add
+            const unsigned same = __match_any_sync(kFull, (static_cast<unsigned long long>(kx) << 32) | ky) &
+                                  __match_any_sync(kFull, kz);
+            const int leader = __ffs(same) - 1;
+            bool pending = have && lane == leader, claimed = false;
+            const unsigned h = dir_hash(kx, ky, kz);
+            int slot = 0;
+            for (int probe = 0; __any_sync(kFull, pending); ++probe) {
+                const int sl = static_cast<int>((h + static_cast<unsigned>(probe)) & (kMergeSlots - 1));
+                if (pending &&
+                    atomicCAS(reinterpret_cast<unsigned *>(&tab[sl].x), kEmptySlot, kx) == kEmptySlot) {
+                    tab[sl].y = dv.y;
+                    tab[sl].z = dv.z;
+                    slot = sl;
+                    pending = false;
+                    claimed = true;
+                }
+                __syncwarp();  // keys claimed this round are complete
+                if (pending) {
+                    const float4 t = tab[sl];
+                    if (__float_as_uint(t.x) == kx && __float_as_uint(t.y) == ky && __float_as_uint(t.z) == kz) {
+                        slot = sl;
+                        pending = false;
+                    }
+                }
+                __syncwarp();
+            }
+            const int my_slot = __shfl_sync(kFull, slot, leader);
+            if (have) atomicAdd(&tab[my_slot].w, cf);
+            used += __popc(__ballot_sync(kFull, claimed));
+            __syncwarp();
+        }
+        if (merge) drain();
+        flush(cur);
+        p = e;
+        if (p < end) cur = advance_cell(F.off, F.n_leaf, cur, p, lane);
+    }
+}
+
 template <int PPL, bool DET>
 __global__ void __launch_bounds__(kBlock, PPL <= 6 ? 3 : 1) cell_accumulate_kernel(const DevGrid G, int l,
                                                                                      const FlushArgs F) {
     __shared__ ulonglong2 sh_rec[kBlock / kWarp][kWarp];
     __shared__ ulonglong2 sh_rec2[kBlock / kWarp][kWarp];
+    __shared__ float4 sh_tab[DET ? 1 : kBlock / kWarp][DET ? 1 : kMergeSlots];
     if (!F.pd->flush) return;
     const long long n = static_cast<long long>(*F.n_sorted);  // records bucketed (holes excluded)
     const long long warps = static_cast<long long>(gridDim.x) * (blockDim.x / kWarp);
@@ -746,7 +920,11 @@ __global__ void __launch_bounds__(kBlock, PPL <= 6 ? 3 : 1) cell_accumulate_kern
     for (long long w = blockIdx.x * static_cast<long long>(blockDim.x / kWarp) + (threadIdx.x >> 5); w < nranges;
          w += warps) {
         const long long beg = w * per, end = min(n, beg + per);
-        accumulate_range<PPL, DET>(G, F, l, beg, end, n, lane, sh_rec[threadIdx.x >> 5], sh_rec2[threadIdx.x >> 5]);
+        if (DET || !DARTRAY_FLUSH_MERGE)
+            accumulate_range<PPL, DET>(G, F, l, beg, end, n, lane, sh_rec[threadIdx.x >> 5], sh_rec2[threadIdx.x >> 5]);
+        else
+            accumulate_range_merged<PPL>(G, F, l, beg, end, n, lane, sh_rec[threadIdx.x >> 5], sh_rec2[threadIdx.x >> 5],
+                                         sh_tab[DET ? 0 : threadIdx.x >> 5]);
     }
 }
 
