@@ -162,7 +162,7 @@ typedef struct dartray_stats {
                              launch's event span on its stream (march_launches of them) */
     int64_t flushes;      /* deposit-record flushes (bucketing + per-cell expansion) that ran,
                              including the one that ends each phase */
-    int64_t batches;      /* source batches traced (both pipelines, restarts excluded) */
+    int64_t batches;      /* source batches traced (all pipelines, restarts excluded) */
     int64_t records;      /* j_sca deposit records written by the ray marcher (one per
                              depositing crossing of steps 2-3 not deposited directly) */
 } dartray_stats;

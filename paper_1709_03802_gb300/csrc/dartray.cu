@@ -66,7 +66,10 @@ int k_hp_host(double g, int n_fwhm, int cap) {
 
 }  // namespace
 
-constexpr int kPipes = 2;
+#ifndef DARTRAY_PIPES
+#define DARTRAY_PIPES 3  // ray pipelines (streams with their own queues and record buffers)
+#endif
+constexpr int kPipes = DARTRAY_PIPES;
 constexpr int kMaxModels = 4096;
 // two-pass segment sums: at most kSegParts parts per segment, kSegPartial partial sums in all
 constexpr int kSegParts = 512;
@@ -722,8 +725,8 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res, bool keep_U = false) 
 
     // Sources are traced in batches (the phase is additive over sources and
     // U_LL is fixed during a phase, so batching does not change the result),
-    // two batches at a time on two streams so that one batch's last waves
-    // overlap the other's.  A batch is sized so that its largest wave fills
+    // kPipes batches at a time on as many streams so that one batch's last waves
+    // overlap the others'.  A batch is sized so that its largest wave fills
     // 80% of a queue, from an estimate of the peak rays per source.  The
     // estimate starts high (small first batches), halves after each batch but
     // never drops below the heaviest batch seen, in this call or an earlier
@@ -734,12 +737,15 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res, bool keep_U = false) 
     const double rps_floor = g->rays_per_src[mode];
     double rays_per_src = rps_floor > 0.0 ? rps_floor
                                           : std::max(static_cast<double>(npix0) * 16.0, g->cap / 64.0);
-    constexpr int kWavesAhead = 6;
+#ifndef DARTRAY_WAVES_AHEAD
+#define DARTRAY_WAVES_AHEAD 6  // waves a pipeline runs per host round trip
+#endif
+    constexpr int kWavesAhead = DARTRAY_WAVES_AHEAD;
     // CUDA graphs of the pipelines' rounds of waves (not in the profile
     // mode, which times every launch with events)
     struct Graphs {
         bool on = false;
-        cudaGraphExec_t exec[kPipes] = {nullptr, nullptr};
+        cudaGraphExec_t exec[kPipes] = {};
         long long launches = 0;
         ~Graphs() {
             for (auto e : exec)
@@ -899,7 +905,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res, bool keep_U = false) 
         }
         for (int i = 0; i < kPipes; ++i) CK(cudaStreamSynchronize(g->pipe[i].stream));
         if (!overflow) {
-            // last records of both pipelines
+            // last records of every pipeline
             for (int i = 0; i < kPipes && mode != MODE_LL; ++i) {
                 if ((rc = enqueue_flush(g, g->pipe[i], dep_pend, 1, tm.get(), i))) return rc;
                 CK(cudaStreamSynchronize(g->pipe[i].stream));
