@@ -114,7 +114,8 @@ typedef struct dartray_params {
     int32_t deposit_direct; /* 1: deposit j_sca with per-pixel atomics only (0: deferred
                                per-cell accumulation of crossing records, atomics only
                                when the record buffer is full) */
-    int64_t deposit_records; /* record buffer capacity; 0 = automatic (0) */
+    int64_t deposit_records; /* record buffer capacity per pipeline; 0 = automatic: 2048 per leaf,
+                                at most 2^29 and about 20 GB per pipeline (0) */
     int32_t deterministic;   /* 1: bit-identical results from run to run: U, the j_sca rows
                                 and the ledger are summed in 64-bit fixed point (exponents
                                 from bounds of each cell's total), so no sum depends on the

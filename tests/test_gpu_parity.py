@@ -325,11 +325,11 @@ def test_deferred_deposit_matches_direct_atomics(records):
 
 def test_galaxy_full_size_sampled_sources():
     """The 297,840-leaf galaxy at full size, in the launch configuration the
-    benchmark uses (both pipelines, automatic queues and record buffers), on
-    a sample the oracle finishes in seconds: every 30000th source of steps
-    1-2 and of one scattering iteration."""
+    benchmark uses (all pipelines, automatic queues, 2^30 deposit records per
+    pipeline), on a sample the oracle finishes in seconds: every 30000th
+    source of steps 1-2 and of one scattering iteration."""
     grid = synth.config2()
-    params = dict(a_rt=0.05, r_pre=0.15 * grid.model_size, src_stride=30000)
+    params = dict(a_rt=0.05, r_pre=0.15 * grid.model_size, src_stride=30000, deposit_records=1 << 30)
     gpu, ref = run_pair(grid, 1, **params)
     led, cnt = ref.stats()
     assert cnt["crossings"] > 1_000_000 and cnt["sources"] > 0
