@@ -62,12 +62,17 @@ def bytes_per_crossing(nl):
 # a deposit record: cell (4 B) and the ray direction with the HG coefficient (16 B)
 RECORD_BYTES = 20
 
+# FP32-pipe figures of the Henyey-Greenstein row expansion (ncu --set full of
+# one flush of the 1/512-source case: profiles/cell_accumulate_galaxy3e5_subset512.md)
+HG_EXPANSION_PIPES = {"kernel": "cell_accumulate_kernel<6, 0>", "fma_pipe_frac": 0.496, "xu_pipe_inst_frac": 0.259,
+                      "issue_active_frac": 0.643, "source": "ncu capture of one flush of a smaller case"}
+
 # DRAM and L2 bytes per crossing of the marcher, summed over all its launches
 # of the 1/30000-source case and divided by that case's crossings (ncu:
 # profiles/march_kernel_traffic_galaxy3e5_subset30000.md); a full-size
 # launch's traffic is taken as these times its crossings.
 MARCH_DRAM_BYTES_PER_CROSSING = 8.24
-MARCH_L2_BYTES_PER_CROSSING = 181.4
+MARCH_L2_BYTES_PER_CROSSING = 180.3
 
 
 def l2_copy_gbs():
@@ -619,7 +624,7 @@ def main():
                 "deposit_records_per_step": float(np.mean([r["records"] for r in results])),
                 "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
                 "gpu_launches": int(sum(r["launches"] for r in results)), "clocks": clocks,
-                "batched_vs_plain": batched, "clumpy_grid": clumpy}
+                "batched_vs_plain": batched, "clumpy_grid": clumpy, "hg_expansion_pipes": HG_EXPANSION_PIPES}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
