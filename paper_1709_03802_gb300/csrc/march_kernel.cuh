@@ -15,6 +15,16 @@ constexpr int kMarchBlock = 128;
 #define DARTRAY_MARCH_MIN_BLOCKS 5
 #endif
 constexpr int kMarchMinBlocks1 = DARTRAY_MARCH_MIN_BLOCKS;  // resident blocks per SM, one wavelength
+#ifndef DARTRAY_MARCH_WIDE_BLOCKS
+#define DARTRAY_MARCH_WIDE_BLOCKS 1  // 0: the register budgets of the first wide build (tuning builds)
+#endif
+// Resident blocks per SM the register budget is set for: 2-4 wavelengths 4
+// (128 registers, at most 12 bytes spilled), 8 wavelengths 3 (170, none
+// spilled), 16 wavelengths 2 (more spill heavily).
+constexpr int march_min_blocks(int nl) {
+    return nl == 1 ? kMarchMinBlocks1
+                   : (DARTRAY_MARCH_WIDE_BLOCKS ? (nl <= 4 ? 4 : (nl == 8 ? 3 : 2)) : (nl <= 4 ? 2 : 1));
+}
 constexpr int kPixTab = 1020;  // pixel centres of levels 0..3 (j_sca levels)
 
 struct MarchArgs {
@@ -162,7 +172,7 @@ struct Ledger {
  *     pixel loop of each depositing lane.
  */
 template <int NL, int MODE, bool DET>
-__global__ void __launch_bounds__(kMarchBlock, NL == 1 ? kMarchMinBlocks1 : (NL <= 4 ? 2 : 1)) march_kernel(const DevGrid G, const MarchArgs A) {
+__global__ void __launch_bounds__(kMarchBlock, march_min_blocks(NL)) march_kernel(const DevGrid G, const MarchArgs A) {
     __shared__ float4 sh_pix[kPixTab];
     __shared__ double sh_led[LG_N][kMaxLambda];
     __shared__ unsigned long long sh_fix[LG_N][kMaxLambda];  // deterministic ledger
