@@ -12,7 +12,7 @@ Metric: ray-cell crossings per second (crossings of steps 1-3 over the step
 time).  Also reported: seconds per scattering iteration.  The L2 cache is
 flushed (a 512 MB write) between timed steps.
 
---impl reference times the FP64 CPU oracle (the reference of this build) on
+--impl reference times the FP64 CPU oracle (the reference implementation) on
 all host cores, one process per core, each on its own bounded sample of the
 same workload (every 30000th source at its own offset, steps 1-2 and one
 scattering iteration per step).  The default run also reports the oracle on
