@@ -82,6 +82,9 @@ typedef struct {
     int32_t max_waves;  /* wave cap per source (error if hit) */
     int32_t src_stride, src_offset; /* process sources with index % stride == offset */
     int32_t octant;     /* 1: octant mode of Sect. 3.6.4 (symmetric models) */
+    int32_t tangent;    /* n > 0: wavelengths [n, 2n) carry the derivative of [0, n) with
+                         * respect to their albedo (forward mode, decisions of the
+                         * wavelengths [0, n) frozen); 0: off */
 } or_params;
 
 /* ledger slots per wavelength */
@@ -557,13 +560,16 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
                  * (Sect. 3.5); I*A_EM is the ray's per-sr luminosity (reading),
                  * Omega_INT = L^2/r^2 (reading). */
                 int all = 1;
-                for (int l = 0; l < nl; ++l) {
+                const int nd = P->tangent > 0 ? P->tangent : nl;  /* wavelengths that decide */
+                for (int l = 0; l < nd; ++l) {
                     const double Iavg = ray->I[l] * fac[l];
                     const double omega_int = L * L / r2;
                     const double dU = Iavg * omega_int * L / (V * c);
                     neg[l] = dU < C->f_u * S->U_LL[(int64_t)leaf * nl + l];
                     all &= neg[l];
                 }
+                /* a derivative deposits where its wavelength does */
+                for (int l = nd; l < nl; ++l) neg[l] = neg[l - nd];
                 if (all) {
                     for (int l = 0; l < nl; ++l) S->ledger[l][LG_BLOCKED] += ray->I[l] * omega_w;
                     S->counters[CT_BLOCK]++;
@@ -600,6 +606,8 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
             }
         }
         /* deposits (Sect. 2; Sect. 3.2 for negligible wavelengths) */
+        double I_in[OR_MAXL];  /* intensities entering the segment */
+        for (int l = 0; l < nl; ++l) I_in[l] = ray->I[l];
         for (int l = 0; l < nl; ++l) {
             const double P_in = ray->I[l] * P_in_unit;
             const double kr = G->kappa_rho[(int64_t)leaf * nl + l];
@@ -612,7 +620,10 @@ static int or_march(or_ctx *C, or_ray *ray, or_list *high, or_list *low) {
                 S->ledger[l][LG_ABSORBED] += (1.0 - w) * lost;
                 S->ledger[l][LG_SCATTERED] += w * lost;
                 if (C->mode != 0) {
-                    const double sca = w * lost;
+                    /* d(w lost)/dw = w dlost/dw + lost for a derivative channel */
+                    const double sca = P->tangent > 0 && l >= P->tangent
+                                           ? w * lost + I_in[l - P->tangent] * P_in_unit * kr * ds * fac[l]
+                                           : w * lost;
                     if (sca > 0) {
                         const int kl = S->k_lam[l];
                         const int npx = 12 << (2 * kl);
@@ -817,6 +828,7 @@ static int or_mirrors(const or_grid *G, const double *leaf_box, const double cen
  * negative error. */
 static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode, int keep_U) {
     if (P->octant && S->dg_on) return -7;  /* the g tally is not folded over mirror images */
+    if (P->tangent > 0 && (P->octant || 2 * P->tangent != G->n_lambda)) return -8;
     const int nl = G->n_lambda;
     or_ctx C;
     memset(&C, 0, sizeof C);
@@ -861,10 +873,11 @@ static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode,
     double centre[3];
     for (int a = 0; a < 3; ++a) centre[a] = G->root_lo[a] + 0.5 * G->nroot[a] * G->root_size;
     int64_t ns = 0;
+    const int nd = P->tangent > 0 ? P->tangent : nl;  /* derivatives do not make sources */
     for (int64_t s = 0; s < nsrc_all; ++s) {
         int on = 0;
         if (s < G->n_leaf) {
-            for (int l = 0; l < nl && !on; ++l) {
+            for (int l = 0; l < nd && !on; ++l) {
                 if (mode == 2) {
                     const int npx = 12 << (2 * S->k_lam[l]);
                     const double *row = pend_cur + S->off_lam[l] + s * npx;
@@ -874,7 +887,7 @@ static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode,
                 }
             }
         } else {
-            for (int l = 0; l < nl; ++l) on |= G->point_lum[(s - G->n_leaf) * nl + l] > 0;
+            for (int l = 0; l < nd; ++l) on |= G->point_lum[(s - G->n_leaf) * nl + l] > 0;
         }
         if (on && (s % P->src_stride) == P->src_offset) {
             ++ns;  /* N_s counts every source of the model */
@@ -1016,10 +1029,11 @@ static int or_phase(const or_grid *G, const or_params *P, or_state *S, int mode,
     }
     if (rc) return rc;
     if (mode >= 1) {
-        double tot = 0;
+        double tot = 0;  /* L_sca,2 of the wavelengths, derivatives excluded */
+        const int64_t n_tot = P->tangent > 0 ? S->off_lam[P->tangent] : S->sca_len;
         for (int64_t i = 0; i < S->sca_len; ++i) {
             S->jsca_total[i] += pend_nxt[i];
-            tot += pend_nxt[i];
+            if (i < n_tot) tot += pend_nxt[i];
         }
         memcpy(S->U_LL, S->U, sizeof(double) * (size_t)G->n_leaf * nl);
         if (mode == 1) S->L_sca2 = tot;
@@ -1069,7 +1083,8 @@ int or_scatter_iter(const or_grid *G, const or_params *P, or_state *S, double *r
     if (rc) return rc;
     const double *nxt = S->cur_is_a ? S->pend_b : S->pend_a;
     double tot = 0;
-    for (int64_t i = 0; i < S->sca_len; ++i) tot += nxt[i];
+    const int64_t n_tot = P->tangent > 0 ? S->off_lam[P->tangent] : S->sca_len;
+    for (int64_t i = 0; i < n_tot; ++i) tot += nxt[i];
     *remaining = S->L_sca2 > 0 ? tot / S->L_sca2 : 0.0;
     return 0;
 }

@@ -78,7 +78,7 @@ class _Params(C.Structure):
                 ("k0", C.c_int32), ("k_ray_max", C.c_int32), ("k_sca_cap", C.c_int32),
                 ("n_fwhm", C.c_int32), ("merge", C.c_int32), ("max_cross", C.c_int32),
                 ("max_waves", C.c_int32), ("src_stride", C.c_int32), ("src_offset", C.c_int32),
-                ("octant", C.c_int32)]
+                ("octant", C.c_int32), ("tangent", C.c_int32)]
 
 
 class _State(C.Structure):
@@ -255,11 +255,14 @@ class OracleParams:
     src_stride: int = 1
     src_offset: int = 0
     octant: int = 0
+    tangent_albedo: int = 0  # 1: also d/d albedo of U (forward mode), see Oracle
 
-    def to_c(self):
+    def to_c(self, n_lambda=1):
         p = _Params()
         for f in dataclasses.fields(self):
-            setattr(p, f.name, getattr(self, f.name))
+            if f.name != "tangent_albedo":
+                setattr(p, f.name, getattr(self, f.name))
+        p.tangent = n_lambda if self.tangent_albedo else 0
         return p
 
 
@@ -270,7 +273,8 @@ class OracleError(RuntimeError):
 _ERRORS = {-1: "out of memory", -2: "crossing cap reached", -3: "wave cap reached",
            -4: "source cell not found", -5: "no progress across a face (inexact grid coordinates)",
            -6: "octant mode: the model is not mirror-symmetric about its centre",
-           -7: "the g tally is not available in the octant mode"}
+           -7: "the g tally is not available in the octant mode",
+           -8: "forward mode: not with the octant mode"}
 
 
 class Oracle:
@@ -278,11 +282,21 @@ class Oracle:
     scatter_iter(), rfed(), jsca(), map()."""
 
     def __init__(self, grid, params: OracleParams | None = None, lib_path=None):
-        self.grid = grid
         self.params = params or OracleParams()
+        self.user_grid = grid
+        self.n_user = grid.n_lambda
+        if self.params.tangent_albedo:
+            # forward mode: wavelengths [n, 2n) are the derivatives of [0, n)
+            # with respect to their albedo -- the same extinction, albedo and
+            # g, no emission of their own; the source of a derivative is the
+            # extra scattered light lost * d(albedo) of its wavelength
+            grid = grid.with_lambda(np.concatenate([grid.kappa_rho, grid.kappa_rho], axis=1),
+                                    np.concatenate([grid.emissivity, np.zeros_like(grid.emissivity)], axis=1),
+                                    np.concatenate([grid.albedo, grid.albedo]), np.concatenate([grid.g, grid.g]))
+        self.grid = grid
         self._lib = _load(lib_path)
         self._g = _GridHandle(grid)
-        self._p = self.params.to_c()
+        self._p = self.params.to_c(self.n_user)
         self._s = _State()
         n = grid.n_leaf * grid.n_lambda
         self.U = np.zeros(n)
@@ -310,7 +324,7 @@ class Oracle:
             self._s.counters[i] = 0
 
     def stats(self):
-        nl = self.grid.n_lambda
+        nl = self.n_user
         led = {name: np.array([self._s.ledger[l][i] for l in range(nl)])
                for i, name in enumerate(LEDGER_NAMES)}
         cnt = {name: int(self._s.counters[i]) for i, name in enumerate(COUNTER_NAMES)}
@@ -367,12 +381,23 @@ class Oracle:
     def rfed(self):
         """U [n_leaf, n_lambda] and absorbed luminosity L_abs = (1-albedo)
         kappa*rho c V U per leaf."""
-        g = self.grid
-        U = self.U.reshape(g.n_leaf, g.n_lambda).copy()
+        g, n = self.grid, self.n_user
+        U = self.U.reshape(g.n_leaf, g.n_lambda)[:, :n].copy()
         V = g.leaf_size ** 3
-        L_abs = (1.0 - g.albedo.astype(np.float64))[None, :] * g.kappa_rho.astype(np.float64) \
+        L_abs = (1.0 - g.albedo[:n].astype(np.float64))[None, :] * g.kappa_rho[:, :n].astype(np.float64) \
             * self.params.c_light * V[:, None] * U
         return U, L_abs
+
+    def rfed_tangent(self):
+        """Forward mode (tangent_albedo): dU/d albedo [n_leaf, n_lambda] with
+        the blocking, splitting and merging decisions frozen, and
+        dL_abs/d albedo = kappa*rho c V ((1 - albedo) dU - U)."""
+        assert self.params.tangent_albedo
+        g, n = self.grid, self.n_user
+        U2 = self.U.reshape(g.n_leaf, g.n_lambda)
+        U, dU = U2[:, :n], U2[:, n:].copy()
+        k = g.kappa_rho[:, :n].astype(np.float64) * self.params.c_light * (g.leaf_size ** 3)[:, None]
+        return dU, k * ((1.0 - g.albedo[:n].astype(np.float64))[None, :] * dU - U)
 
     def pending_next(self):
         ptr = self._lib.or_pending_next(C.byref(self._s))
