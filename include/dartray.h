@@ -131,6 +131,16 @@ typedef struct dartray_params {
     int32_t graphs;          /* 1: each pipeline's rounds of waves (ray march, merge, deposit
                                 flush, wave advance) are captured once per phase as a CUDA
                                 graph and replayed; ignored with profile = 1 (1) */
+    int32_t tangent_albedo;  /* 1: forward mode -- the sweep also carries, for every
+                                wavelength, the derivative of U with respect to its albedo
+                                (dartray_rfed_tangent), as extra wavelengths with the same
+                                extinction, albedo and g, no emission of their own, the
+                                light their wavelength loses in each segment as extra
+                                scattering source (d(albedo lost)/d albedo, Sect. 2), and
+                                the blocking, splitting and merging decisions of their
+                                wavelength (frozen).  At most 8 wavelengths; single-model
+                                grids outside the octant and deterministic modes; no state
+                                files (0) */
 } dartray_params;
 
 /* Per-call statistics.  Ledger entries are luminosities per wavelength of the
@@ -355,6 +365,13 @@ int dartray_autotune(dartray_grid *grid, int32_t sample_stride, int32_t *choice,
  * L_abs = (1 - albedo) * kappa_rho * c_light * V * U [n_leaf][n_lambda]
  * (either pointer may be NULL), written to host or device memory. */
 int dartray_rfed(dartray_grid *grid, float *U, float *L_abs, int dst_is_device);
+
+/* Forward mode (params.tangent_albedo): dU/d albedo [n_leaf][n_lambda] (the
+ * derivative of each wavelength's U with respect to its own albedo, the
+ * sweep's decisions held) and dL_abs/d albedo = kappa_rho c_light V
+ * ((1 - albedo) dU - U), host or device memory (either may be NULL).
+ * Errors: INVAL, STATE (not the forward mode), CUDA. */
+int dartray_rfed_tangent(dartray_grid *grid, float *dU, float *dL_abs, int dst_is_device);
 
 /* j_sca layout: k_lambda per wavelength, offset of each wavelength block and
  * total length; block l is [n_leaf][12 * 4^k_lambda[l]] (nested pixels). */

@@ -252,6 +252,26 @@ int copy_out_cols(float *dst, const float *src, size_t rows, int nlu, int nl, bo
     return DARTRAY_OK;
 }
 
+// The caller's [rows][nlu] into columns [col0, col0 + nlu) of [rows][nl]
+// (the other columns untouched).
+int copy_in_cols_at(float *dst, const float *src, size_t rows, int nlu, int nl, int col0, bool on_device,
+                    cudaStream_t s) {
+    if (rows == 0) return DARTRAY_OK;
+    if (!src) return fail(DARTRAY_E_INVAL, "missing input array");
+    CK(cudaMemcpy2DAsync(dst + col0, nl * sizeof(float), src, nlu * sizeof(float), nlu * sizeof(float), rows,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return DARTRAY_OK;
+}
+
+// Columns [col0, col0 + nlu) of the library's [rows][nl] to the caller's [rows][nlu].
+int copy_out_cols_at(float *dst, const float *src, size_t rows, int nlu, int nl, int col0, bool dst_is_device,
+                     cudaStream_t s) {
+    if (rows == 0) return DARTRAY_OK;
+    CK(cudaMemcpy2DAsync(dst, nlu * sizeof(float), src + col0, nl * sizeof(float), nlu * sizeof(float), rows,
+                         dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    return DARTRAY_OK;
+}
+
 // the marcher width for n wavelengths
 int padded_lambda(int n) { return n <= 1 ? 1 : (n <= 2 ? 2 : (n <= 4 ? 4 : (n <= 8 ? 8 : 16))); }
 
@@ -1025,7 +1045,7 @@ int run_phase(dartray_grid *g, int mode, PhaseResult *res, bool keep_U = false) 
         CK(cudaStreamSynchronize(s));
         for (int m = 0; m < g->n_models; ++m) {
             double t = 0.0;
-            for (int l = 0; l < g->nl; ++l) t += seg[m * g->nl + l];
+            for (int l = 0; l < g->nlu; ++l) t += seg[m * g->nl + l];  // derivatives and padding excluded
             res->pend_sum += t;
             if (mode == MODE_DIRECT) g->m_lsca2[m] = t;
             g->m_rem[m] = g->m_lsca2[m] > 0 ? t / g->m_lsca2[m] : 0.0;
@@ -1117,6 +1137,7 @@ int dartray_params_default(dartray_params *p) {
     p->deterministic = 0;
     p->octant = 0;
     p->graphs = 1;
+    p->tangent_albedo = 0;
     return DARTRAY_OK;
 }
 
@@ -1151,7 +1172,11 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
     else dartray_params_default(&P);
     const int nlu = desc->n_lambda;
     if (nlu < 1 || nlu > 16) return fail(DARTRAY_E_INVAL, "n_lambda must be in [1, 16]");
-    const int nl = padded_lambda(nlu);
+    // forward mode: the derivatives with respect to the albedo ride in the
+    // upper half of the padded wavelengths, [nl/2, nl/2 + nlu)
+    const bool tangent = params && params->tangent_albedo == 1;
+    if (tangent && nlu > 8) return fail(DARTRAY_E_INVAL, "the forward mode takes at most 8 wavelengths");
+    const int nl = tangent ? 2 * padded_lambda(nlu) : padded_lambda(nlu);
     long long tot_leaf = 0, tot_nodes = 0, tot_point = 0;
     for (int m = 0; m < n_models; ++m) {
         const dartray_grid_desc &d = descs[m];
@@ -1168,9 +1193,12 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
         P.src_offset >= P.src_stride || P.max_cross < 1 || P.max_waves < 1 ||
         (P.queue_rays != 0 && P.queue_rays < 1024) || P.deposit_records < 0 ||
         !(P.c_light > 0) || P.a_rt < 0 || P.deterministic < 0 || P.deterministic > 1 || P.octant < 0 ||
-        P.octant > 1 || (P.octant && P.src_stride != 1) || P.graphs < 0 || P.graphs > 1)
+        P.octant > 1 || (P.octant && P.src_stride != 1) || P.graphs < 0 || P.graphs > 1 || P.tangent_albedo < 0 ||
+        P.tangent_albedo > 1)
         return fail(DARTRAY_E_INVAL, "invalid parameters");
     if (P.octant && n_models > 1) return fail(DARTRAY_E_INVAL, "the octant mode takes a single model");
+    if (tangent && (n_models > 1 || P.octant || P.deterministic))
+        return fail(DARTRAY_E_INVAL, "the forward mode takes a single model, outside the octant and deterministic modes");
     if (n_models > 1 && static_cast<long long>(n_models) * LG_N * nl * 8 > 32768)
         return fail(DARTRAY_E_INVAL, "a batch holds at most 4096 / (6 n_lambda) models");
     const bool on_dev = desc->inputs_on_device != 0;
@@ -1191,6 +1219,11 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
     }
     alb.resize(nl, 0.f);  // the extra wavelengths: no scattering, isotropic
     gg.resize(nl, 0.f);
+    if (tangent)  // a derivative has its wavelength's albedo and g
+        for (int l = 0; l < nlu; ++l) {
+            alb[nl / 2 + l] = alb[l];
+            gg[nl / 2 + l] = gg[l];
+        }
 
     dartray_grid *g = new dartray_grid();
     g->P = P;
@@ -1421,6 +1454,7 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
         const bool dev_m = d.inputs_on_device != 0;
         const size_t l0 = static_cast<size_t>(g->m_leaf0[m]) * nl, p0 = static_cast<size_t>(g->m_point0[m]);
         if ((rc = copy_in_cols(g->d_kr + l0, d.kappa_rho, d.n_leaf, nlu, nl, dev_m, s)) ||
+            (tangent && (rc = copy_in_cols_at(g->d_kr + l0, d.kappa_rho, d.n_leaf, nlu, nl, nl / 2, dev_m, s))) ||
             (rc = copy_in_cols(g->d_emis + l0, d.emissivity, d.n_leaf, nlu, nl, dev_m, s)) ||
             (rc = copy_in(g->d_pxyz + 3 * p0, d.point_xyz, 3ull * d.n_point, dev_m, s)) ||
             (rc = copy_in_cols(g->d_plum + p0 * nl, d.point_lum, d.n_point, nlu, nl, dev_m, s)))
@@ -1469,6 +1503,7 @@ int create_grid(const dartray_grid_desc *descs, int n_models, const dartray_para
     G.n_leaf = static_cast<int>(tot_leaf);
     G.nl = nl;
     G.nl_user = nlu;
+    G.tangent = tangent ? 1 : 0;
     G.n_point = static_cast<int>(tot_point);
     G.n_models = n_models;
     G.models = g->d_models;
@@ -1803,6 +1838,9 @@ int dartray_set_kappa_rho(dartray_grid *g, const float *kappa_rho, int src_is_de
     int rc = set_device(g);
     if (rc) return rc;
     if ((rc = copy_in_cols(g->d_kr, kappa_rho, g->n_leaf, g->nlu, g->nl, src_is_device != 0, g->stream))) return rc;
+    if (g->G.tangent &&
+        (rc = copy_in_cols_at(g->d_kr, kappa_rho, g->n_leaf, g->nlu, g->nl, g->nl / 2, src_is_device != 0, g->stream)))
+        return rc;
     CK(cudaStreamSynchronize(g->stream));
     return DARTRAY_OK;
 }
@@ -1979,6 +2017,29 @@ int dartray_rfed(dartray_grid *g, float *U, float *L_abs, int dst_is_device) {
     return DARTRAY_OK;
 }
 
+int dartray_rfed_tangent(dartray_grid *g, float *dU, float *dL_abs, int dst_is_device) {
+    g_last_error.clear();
+    if (!g) return fail(DARTRAY_E_INVAL, "null grid");
+    if (!g->G.tangent) return fail(DARTRAY_E_STATE, "the grid was not created in the forward mode");
+    int rc = set_device(g);
+    if (rc) return rc;
+    const int half = g->nl / 2;
+    if (dU && (rc = copy_out_cols_at(dU, g->d_U, g->n_leaf, g->nlu, g->nl, half, dst_is_device != 0, g->stream)))
+        return rc;
+    if (dL_abs) {
+        const size_t n = static_cast<size_t>(g->n_leaf) * g->nlu;
+        float *dst = dL_abs;
+        if (!dst_is_device && (rc = stage_buffer(g, n, &dst))) return rc;
+        tangent_labs_kernel<<<static_cast<unsigned>((n + kBlock - 1) / kBlock), kBlock, 0, g->stream>>>(
+            g->G, g->d_U, static_cast<float>(g->P.c_light), dst);
+        ++g->launches;
+        CK(cudaGetLastError());
+        if (!dst_is_device) CK(cudaMemcpyAsync(dL_abs, dst, n * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    return DARTRAY_OK;
+}
+
 int dartray_jsca_layout(const dartray_grid *g, int32_t *k_lambda, int64_t *offsets, int64_t *total_len) {
     if (!g) return fail(DARTRAY_E_INVAL, "null grid");
     for (int l = 0; l < g->nlu; ++l) {
@@ -2094,7 +2155,8 @@ int dartray_map_noalloc(dartray_grid *g, const double observer[3], int32_t nside
 int dartray_state_save(dartray_grid *g, const char *path) {
     g_last_error.clear();
     if (!g || !path) return fail(DARTRAY_E_INVAL, "null argument");
-    if (g->n_models > 1) return fail(DARTRAY_E_INVAL, "state files hold single-model grids");
+    if (g->n_models > 1 || g->G.tangent)
+        return fail(DARTRAY_E_INVAL, "state files hold single-model grids outside the forward mode");
     int rc = set_device(g);
     if (rc) return rc;
     const size_t nU = static_cast<size_t>(g->n_leaf) * g->nlu;
@@ -2127,7 +2189,8 @@ int dartray_state_save(dartray_grid *g, const char *path) {
 int dartray_state_load(dartray_grid *g, const char *path) {
     g_last_error.clear();
     if (!g || !path) return fail(DARTRAY_E_INVAL, "null argument");
-    if (g->n_models > 1) return fail(DARTRAY_E_INVAL, "state files hold single-model grids");
+    if (g->n_models > 1 || g->G.tangent)
+        return fail(DARTRAY_E_INVAL, "state files hold single-model grids outside the forward mode");
     int rc = set_device(g);
     if (rc) return rc;
     const size_t nU = static_cast<size_t>(g->n_leaf) * g->nlu;

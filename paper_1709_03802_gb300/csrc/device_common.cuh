@@ -34,6 +34,7 @@ struct DevGrid {
     float root_size;
     int n_nodes, n_leaf, nl, n_point;
     int nl_user;                // the caller's wavelengths: [0, nl_user); the rest pad nl
+    int tangent;                // 1: [nl/2, nl/2 + nl_user) carry d/d albedo of [0, nl_user)
     const int32_t *node_child;  // first child, or -(leaf+1)
     const float4 *node_box;     // lo.xyz, side
     const float4 *leaf_box;

@@ -520,6 +520,15 @@ __global__ void __launch_bounds__(kMarchBlock, march_min_blocks(NL)) march_kerne
                             neg[l] = I[l] * fac[l] < ull[l] * (r2f * A.c_light);
                             all = all && neg[l];
                         }
+                        // forward mode: a derivative (upper half, infinite
+                        // threshold, so out of the test above) deposits where
+                        // its wavelength does
+                        if constexpr (NL >= 2) {
+                            if (G.tangent) {
+#pragma unroll
+                                for (int l = NL / 2; l < NL; ++l) neg[l] = neg[l - NL / 2];
+                            }
+                        }
                         if (all) {
                             float tmp[NL];
 #pragma unroll
@@ -559,10 +568,12 @@ __global__ void __launch_bounds__(kMarchBlock, march_min_blocks(NL)) march_kerne
                     }
                 }
                 if (outcome == 0) {
+                    float lostv[NL];  // P_in (1 - T) of the segment, per wavelength
 #pragma unroll
                     for (int l = 0; l < NL; ++l) {
                         const float P_in = I[l] * omega_k;
                         const float lost = P_in * kr[l] * ds * fac[l];
+                        lostv[l] = lost;
                         if (neg[l]) {
                             acc_skip[l] += lost;
                         } else {
@@ -576,6 +587,15 @@ __global__ void __launch_bounds__(kMarchBlock, march_min_blocks(NL)) march_kerne
                             acc_dep[l] += lost;
                         }
                         I[l] *= T[l];
+                    }
+                    // forward mode: d(albedo lost)/d albedo adds the light its
+                    // wavelength lost over the segment (entering intensity)
+                    if constexpr (NL >= 2 && MODE != MODE_LL) {
+                        if (G.tangent) {
+#pragma unroll
+                            for (int l = NL / 2; l < NL; ++l)
+                                if (!neg[l]) sca[l] += lostv[l - NL / 2] / Z[l - NL / 2];
+                        }
                     }
                 }
             }

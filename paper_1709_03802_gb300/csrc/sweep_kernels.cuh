@@ -198,7 +198,7 @@ __global__ void source_flags_kernel(const DevGrid G, int mode, const float *pend
     if (s >= n_all) return;
     int on = 0;
     if (s < G.n_leaf) {
-        for (int l = 0; l < G.nl && !on; ++l) {
+        for (int l = 0; l < G.nl_user && !on; ++l) {  // padding and derivatives make no sources
             if (mode == MODE_SCATTER) {
                 const int np = 12 << (2 * G.k_lam[l]);
                 const float *row = pend_src + G.off_lam[l] + static_cast<long long>(s) * np;
@@ -209,7 +209,7 @@ __global__ void source_flags_kernel(const DevGrid G, int mode, const float *pend
             }
         }
     } else {
-        for (int l = 0; l < G.nl; ++l) on |= G.point_lum[static_cast<long long>(s - G.n_leaf) * G.nl + l] > 0.f;
+        for (int l = 0; l < G.nl_user; ++l) on |= G.point_lum[static_cast<long long>(s - G.n_leaf) * G.nl + l] > 0.f;
     }
     if (on && model_active) {
         // batched grids: models that have converged emit nothing more
@@ -1100,6 +1100,17 @@ __global__ void segment_finish_kernel(const double *partial, int nseg, int parts
     double s = 0.0;
     for (int p = 0; p < parts; ++p) s += partial[static_cast<long long>(seg) * parts + p];
     out[seg] = s;
+}
+
+// Forward mode: dL_abs/d albedo = kappa*rho c V ((1 - albedo) dU - U), the
+// caller's [n_leaf][nl_user] layout (U at column l, dU at nl/2 + l).
+__global__ void tangent_labs_kernel(const DevGrid G, const float *U, float c_light, float *out) {
+    const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i >= static_cast<long long>(G.n_leaf) * G.nl_user) return;
+    const int c = static_cast<int>(i / G.nl_user), l = static_cast<int>(i % G.nl_user);
+    const float L = G.leaf_box[c].w;
+    const long long r = static_cast<long long>(c) * G.nl;
+    out[i] = G.kappa_rho[r + l] * c_light * (L * L * L) * ((1.f - G.albedo[l]) * U[r + G.nl / 2 + l] - U[r + l]);
 }
 
 // j_sca_total += pending, in place.

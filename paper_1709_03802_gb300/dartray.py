@@ -43,7 +43,7 @@ class dartray_params(C.Structure):
                 ("src_stride", C.c_int32), ("src_offset", C.c_int32), ("queue_rays", C.c_int64),
                 ("src_batch", C.c_int64), ("profile", C.c_int32), ("deposit_direct", C.c_int32),
                 ("deposit_records", C.c_int64), ("deterministic", C.c_int32), ("octant", C.c_int32),
-                ("graphs", C.c_int32)]
+                ("graphs", C.c_int32), ("tangent_albedo", C.c_int32)]
 
 
 _L = MAX_LAMBDA
@@ -117,6 +117,7 @@ def load(build_if_missing=True):
         "dartray_set_kappa_rho": ([P, P, C.c_int], C.c_int),
         "dartray_jsca_dg_arm": ([P, P], C.c_int),
         "dartray_jsca_dg": ([P, P, C.c_int], C.c_int),
+        "dartray_rfed_tangent": ([P, P, P, C.c_int], C.c_int),
         "dartray_state_load": ([P, C.c_char_p], C.c_int),
         "dartray_grid_destroy": ([P], None),
         "dartray_last_error": ([], C.c_char_p),
@@ -135,7 +136,7 @@ EXPORTED = ("dartray_params_default", "dartray_grid_create", "dartray_direct", "
             "dartray_grid_create_batch", "dartray_model_info", "dartray_model_stats", "dartray_autotune",
             "dartray_dust_emission", "dartray_set_emissivity", "dartray_direct_incremental",
             "dartray_map_external", "dartray_map_external_vjp", "dartray_set_kappa_rho",
-            "dartray_jsca_dg_arm", "dartray_jsca_dg")
+            "dartray_jsca_dg_arm", "dartray_jsca_dg", "dartray_rfed_tangent")
 
 
 def _check(rc):
@@ -360,6 +361,17 @@ class DartRay:
             out = np.empty(self.sca_len, np.float32)
         dartray_jsca(self._h, 0 if which == "total" else 1, _ptr(out), dev)
         return out
+
+    def rfed_tangent(self, dU=None, dL_abs=None):
+        """Forward mode (tangent_albedo=1): dU/d albedo and dL_abs/d albedo
+        [n_leaf][n_lambda] (dartray_rfed_tangent), into the given host arrays
+        or CUDA tensors (both of one kind) or new host arrays."""
+        dev = _is_cuda_tensor(dU) or _is_cuda_tensor(dL_abs)
+        if not dev:
+            dU = np.empty((self.n_leaf, self.n_lambda), np.float32) if dU is None else dU
+            dL_abs = np.empty((self.n_leaf, self.n_lambda), np.float32) if dL_abs is None else dL_abs
+        _check(load().dartray_rfed_tangent(self._h, _ptr(dU), _ptr(dL_abs), int(dev)))
+        return dU, dL_abs
 
     def jsca_block(self, l, which="total"):
         a = self.jsca(which)

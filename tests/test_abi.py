@@ -110,6 +110,24 @@ def test_rejects_unsupported_lambda_count(n):
     assert rc == -1 and "n_lambda" in msg
 
 
+@pytest.mark.parametrize("case", ["deterministic", "nine_wavelengths"])
+def test_forward_mode_rejections(case):
+    """The forward mode (tangent_albedo) takes at most 8 wavelengths and no
+    deterministic mode; both are refused before any device work."""
+    grid = synth.config1()
+    d, keep = _desc(grid)
+    p = dr.dartray_params()
+    dr.load().dartray_params_default(C.byref(p))
+    p.tangent_albedo = 1
+    if case == "deterministic":
+        p.deterministic = 1
+    else:
+        d.n_lambda = 9
+    h = C.c_void_p()
+    rc = dr.load().dartray_grid_create(C.byref(d), C.byref(p), None, C.byref(h))
+    assert rc == -1 and "forward mode" in dr.load().dartray_last_error().decode()
+
+
 def _c_layout(struct, fields, tmp_path):
     """sizeof and offsetof of a header struct, from a C program built with
     the system compiler against include/dartray.h."""
