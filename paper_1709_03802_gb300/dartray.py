@@ -594,3 +594,41 @@ def external_map(model, kappa_rho, view, up, origin, pixel, nx, ny, use_jsca=Tru
             return gk, ga, gg
 
     return _ExternalMap.apply(kappa_rho, albedo, g)
+
+
+def rfed_albedo(model, albedo):
+    """U and L_abs [n_leaf][n_lambda] (CUDA tensors) of `model`, a DartRay
+    created with tangent_albedo=1 whose sweep has run, as functions of
+    `albedo` (a CUDA tensor [n_lambda] holding the model's albedo): the
+    backward pass contracts the upstream gradients with the forward-mode
+    derivatives dU/d albedo and dL_abs/d albedo of the library's sweep (each
+    wavelength depends on its own albedo only)."""
+    import torch
+
+    if not np.allclose(albedo.detach().cpu().numpy(), np.asarray(model.grid.albedo, np.float64), rtol=1e-6, atol=0):
+        raise ValueError("albedo must hold the model's values (the sweep ran with them)")
+
+    class _RfedAlbedo(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, alb):
+            shape = (model.n_leaf, model.n_lambda)
+            U = torch.empty(shape, dtype=torch.float32, device=alb.device)
+            L = torch.empty_like(U)
+            dU = torch.empty_like(U)
+            dL = torch.empty_like(U)
+            model.rfed(U, L)
+            model.rfed_tangent(dU, dL)
+            ctx.save_for_backward(dU, dL)
+            return U, L
+
+        @staticmethod
+        def backward(ctx, gU, gL):
+            dU, dL = ctx.saved_tensors
+            g = torch.zeros(dU.shape[1], dtype=torch.float64, device=dU.device)
+            if gU is not None:
+                g += (gU.double() * dU.double()).sum(0)
+            if gL is not None:
+                g += (gL.double() * dL.double()).sum(0)
+            return g.float()
+
+    return _RfedAlbedo.apply(albedo)

@@ -95,3 +95,44 @@ def test_tangent_rejections(tmp_path):
     p = DartRay(g, r_pre=0.5)
     with pytest.raises(DartRayError):
         p.rfed_tangent()
+
+
+def test_rfed_albedo_autograd_against_central_differences():
+    """A loss of U and L_abs through torch.autograd (rfed_albedo) against
+    central differences of the same loss over deterministic sweeps at
+    albedo (1 +- 1e-2), no blocking."""
+    from paper_1709_03802_gb300 import rfed_albedo
+    g = two_lambda_cube()
+
+    def sweep(grid, **kw):
+        m = DartRay(grid, a_rt=0.0, r_pre=0.5, **kw)
+        m.direct()
+        for _ in range(2):
+            m.scatter_iter()
+        return m
+
+    rng = np.random.default_rng(1709 * 100 + 46)
+    w = torch.tensor(rng.uniform(0.5, 1.5, (g.n_leaf, 2)), device="cuda")
+
+    t = sweep(g, tangent_albedo=1)
+    alb = torch.tensor(g.albedo, device="cuda", requires_grad=True)
+    U, L = rfed_albedo(t, alb)
+    S = float(U.detach().max())  # a fixed scale
+
+    def loss(U, L):
+        return (w * U.double() ** 2).sum() / S + L.double().sum()
+
+    loss(U, L).backward()
+    for l in range(2):
+        vals = []
+        for sgn in (1, -1):
+            a = g.albedo.copy()
+            a[l] *= 1 + sgn * 1e-2
+            gp = g.with_lambda(g.kappa_rho, g.emissivity, a, g.g)
+            m = sweep(gp, deterministic=1)
+            Up, Lp = m.rfed()
+            val = loss(torch.tensor(Up, device="cuda"), torch.tensor(Lp, device="cuda"))
+            vals.append((float(val), float(gp.albedo[l])))
+        fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+        print(f"d loss / d albedo[{l}]: autograd {float(alb.grad[l]):.6e}, central differences {fd:.6e}")
+        assert abs(float(alb.grad[l]) - fd) <= REL_CELL * abs(fd)
