@@ -28,6 +28,11 @@
  *                     (Eq. 10).
  *   Sect. 2 (end), 3.6.3  maps for an observer inside the model:
  *                     I_obs = I_0 exp(-tau).
+ *   Sect. 3.6.4       the 2D (octant) mode for mirror-symmetric models.
+ * Beyond the paper's sweep, for checking the library's derivatives: the
+ * derivative with respect to g of the j_sca pixel toward a distant observer
+ * (a tally at every deposit), and a forward mode in which extra wavelengths
+ * carry the derivative of U with respect to the albedo.
  * Readings of passages the paper leaves open are marked "reading".
  *
  * HEALPix is written from its published definition (Gorski et al. 2005): 12
