@@ -152,6 +152,48 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def roofline_of(prof, nl, peak, peak_src, l2_peak=None):
+    """The roofline object of the marcher from a profiled step (prof: the
+    summed stats of run_step with params.profile = 1 and the step's time).
+
+    Algorithmic bytes: per crossing (leaf box, face link, node word,
+    kappa*rho, U_LL, U read-modify-write) plus one deposit record per
+    depositing crossing.  The marcher's launches run on three pipeline
+    streams at once, so their CUDA-event spans overlap: the time the kernel
+    holds the GPU is the union of the spans (march_ms), and achieved = all
+    its algorithmic bytes / that union.  The per-launch figure (bytes /
+    summed spans, each span including the wait for SMs that the other
+    pipelines' launches hold) is kept beside it."""
+    alg_bytes = prof["march_crossings"] * bytes_per_crossing(nl) + RECORD_BYTES * prof["records"]
+    march_sum_ms, launches = prof["march_sum_ms"], prof["march_launches"]
+    union_ms = prof["march_ms"]
+    achieved = alg_bytes / (union_ms / 1e3) / 1e9 if union_ms > 0 else None
+    per_span = alg_bytes / (march_sum_ms / 1e3) / 1e9 if march_sum_ms > 0 else None
+    per_launch = prof["march_crossings"] / launches if launches else 0.0
+    traffic = MARCH_DRAM_BYTES_PER_CROSSING * per_launch if MARCH_DRAM_BYTES_PER_CROSSING else None
+    l2 = None
+    if MARCH_L2_BYTES_PER_CROSSING and union_ms > 0 and l2_peak:
+        l2_ach = MARCH_L2_BYTES_PER_CROSSING * prof["march_crossings"] / (union_ms / 1e3) / 1e9
+        l2 = {"achieved": l2_ach, "peak": l2_peak, "unit": "GB/s", "frac": l2_ach / l2_peak,
+              "bytes_per_crossing": MARCH_L2_BYTES_PER_CROSSING,
+              "peak_source": "measured here: L2-resident device copy (48 MiB moved per copy)"}
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "traffic_note": "ncu DRAM bytes per crossing of the small case times the crossings of an "
+                            "average full-size launch" if traffic else None,
+            "l2": l2,
+            "kernel": "march_kernel (ray marcher)", "peak_source": peak_src,
+            "launches": launches, "avg_launch_ms": march_sum_ms / launches if launches else None,
+            "bytes_per_crossing": bytes_per_crossing(nl), "record_bytes": RECORD_BYTES,
+            "crossings_profiled_step": prof["march_crossings"], "records_profiled_step": prof["records"],
+            "achieved_over_summed_launch_spans": per_span,
+            "frac_over_summed_launch_spans": per_span / peak if per_span else None,
+            "time_basis": "union of the marcher's launch spans on its three pipeline streams",
+            "kernel_busy_share_of_step": prof["march_ms"] / prof["step_ms"],
+            "deposit_flush_share_of_step": prof["flush_ms"] / prof["step_ms"],
+            "note": "from warm-up step 2, whose launches are timed with CUDA events"}
+
+
 def max_over_ranks(value, dist, device):
     """Largest value over the ranks of the process group (the job's time is
     the slowest replica's); `dist` None means a single process."""
@@ -563,44 +605,7 @@ def main():
     peak, peak_src = peaks()
     roofline = None
     if prof is not None:
-        # algorithmic bytes of the marcher in the profiled step: per crossing
-        # (leaf box, face link, node word, kappa*rho, U_LL, U read-modify-write)
-        # plus one deposit record per depositing crossing
-        alg_bytes = prof["march_crossings"] * bytes_per_crossing(nl) + RECORD_BYTES * prof["records"]
-        # The marcher's launches run on three pipeline streams at once, so
-        # their CUDA-event spans overlap: the time the kernel holds the GPU is
-        # the union of the spans (march_ms), and achieved = all its algorithmic
-        # bytes / that union.  The per-launch figure (bytes / summed spans,
-        # each span including the wait for SMs that the other pipelines'
-        # launches hold) is kept beside it.
-        march_sum_ms, launches = prof["march_sum_ms"], prof["march_launches"]
-        union_ms = prof["march_ms"]
-        achieved = alg_bytes / (union_ms / 1e3) / 1e9 if union_ms > 0 else None
-        per_span = alg_bytes / (march_sum_ms / 1e3) / 1e9 if march_sum_ms > 0 else None
-        per_launch = prof["march_crossings"] / launches if launches else 0.0
-        traffic = MARCH_DRAM_BYTES_PER_CROSSING * per_launch if MARCH_DRAM_BYTES_PER_CROSSING else None
-        l2 = None
-        if MARCH_L2_BYTES_PER_CROSSING and union_ms > 0:
-            l2_peak = l2_copy_gbs()
-            l2_ach = MARCH_L2_BYTES_PER_CROSSING * prof["march_crossings"] / (union_ms / 1e3) / 1e9
-            l2 = {"achieved": l2_ach, "peak": l2_peak, "unit": "GB/s", "frac": l2_ach / l2_peak,
-                  "bytes_per_crossing": MARCH_L2_BYTES_PER_CROSSING,
-                  "peak_source": "measured here: L2-resident device copy (48 MiB moved per copy)"}
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                    "traffic_note": "ncu DRAM bytes per crossing of the small case times the crossings of an "
-                                    "average full-size launch" if traffic else None,
-                    "l2": l2,
-                    "kernel": "march_kernel (ray marcher)", "peak_source": peak_src,
-                    "launches": launches, "avg_launch_ms": march_sum_ms / launches if launches else None,
-                    "bytes_per_crossing": bytes_per_crossing(nl), "record_bytes": RECORD_BYTES,
-                    "crossings_profiled_step": prof["march_crossings"], "records_profiled_step": prof["records"],
-                    "achieved_over_summed_launch_spans": per_span,
-                    "frac_over_summed_launch_spans": per_span / peak if per_span else None,
-                    "time_basis": "union of the marcher's launch spans on its three pipeline streams",
-                    "kernel_busy_share_of_step": prof["march_ms"] / prof["step_ms"],
-                    "deposit_flush_share_of_step": prof["flush_ms"] / prof["step_ms"],
-                    "note": "from warm-up step 2, whose launches are timed with CUDA events"}
+        roofline = roofline_of(prof, nl, peak, peak_src, l2_copy_gbs() if MARCH_L2_BYTES_PER_CROSSING else None)
     gpu.close()
     batched = clumpy = None
     if not args.no_batched and args.src_stride == 1:

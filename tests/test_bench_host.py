@@ -39,3 +39,20 @@ def test_algorithmic_bytes_per_crossing():
     # U read-modify-write per wavelength
     assert bench.bytes_per_crossing(1) == 60
     assert bench.bytes_per_crossing(4) == 44 + 16 * 4
+
+
+def test_roofline_of_a_profiled_step():
+    """achieved = algorithmic bytes / the union of the marcher's spans; the
+    per-launch figure over the summed spans; DRAM traffic per average launch
+    and L2 bytes from the per-crossing figures."""
+    prof = {"march_crossings": 1e12, "records": 3e11, "march_sum_ms": 60000.0, "march_launches": 20000,
+            "march_ms": 40000.0, "step_ms": 65000.0, "flush_ms": 30000.0}
+    r = bench.roofline_of(prof, 1, 6000.0, "of measured", l2_peak=7000.0)
+    alg = 1e12 * 60 + 3e11 * bench.RECORD_BYTES
+    assert abs(r["achieved"] - alg / 40.0 / 1e9) < 1e-6 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / 6000.0) < 1e-12
+    assert abs(r["achieved_over_summed_launch_spans"] - alg / 60.0 / 1e9) < 1e-6 * r["achieved"]
+    assert abs(r["traffic"] - bench.MARCH_DRAM_BYTES_PER_CROSSING * 1e12 / 20000) < 1.0
+    assert abs(r["l2"]["achieved"] - bench.MARCH_L2_BYTES_PER_CROSSING * 1e12 / 40.0 / 1e9) < 1e-6
+    assert abs(r["kernel_busy_share_of_step"] - 40000 / 65000) < 1e-12
+    assert bench.roofline_of(prof, 1, 6000.0, "of measured")["l2"] is None
