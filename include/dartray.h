@@ -178,8 +178,10 @@ typedef struct dartray_stats {
                              depositing crossing of steps 2-3 not deposited directly) */
 } dartray_stats;
 
-/* Fill *p with the defaults above (r_pre is set when the grid is created if
- * left negative). */
+/* Fill *p with the defaults above -- the paper's input-defined values of
+ * Sect. 2 (R_pre, f_L), Sect. 3.1 (N_rays, N_rays^max, n_FWHM, the k cap) and
+ * Sect. 3.5 (a_RT); r_pre is set when the grid is created if left
+ * negative.  Errors: INVAL (NULL). */
 int dartray_params_default(dartray_params *p);
 
 /*
@@ -219,14 +221,15 @@ int dartray_grid_create_batch(const dartray_grid_desc *descs, int32_t n_models, 
 
 /* Layout and state of model `model` of a grid (a single-model grid has
  * model 0): first leaf and number of leaves, first point source, remaining
- * scattered fraction after the last call, 1 while it still emits in
+ * scattered fraction after the last call (the stop test of Sect. 2 against
+ * the model's own step-2 scattered luminosity), 1 while it still emits in
  * scattering iterations.  Any pointer may be NULL.  Errors: INVAL. */
 int dartray_model_info(const dartray_grid *grid, int32_t model, int64_t *leaf_offset, int32_t *n_leaf,
                        int64_t *point_offset, double *remaining_frac, int32_t *active);
 
-/* Ledger of model `model` for the last phase of the last call, its f_U and
- * its scattered luminosity at the end of step 2 (other fields 0).  Errors:
- * INVAL. */
+/* Ledger of model `model` for the last phase of the last call, its f_U
+ * (Eq. 10 with the model's own N_s) and its scattered luminosity at the end
+ * of step 2 (Sect. 2; other fields 0).  Errors: INVAL. */
 int dartray_model_stats(const dartray_grid *grid, int32_t model, dartray_stats *stats);
 
 /* Steps 1 and 2 of Sect. 2: U_LL within R_pre, then direct light with ray
@@ -303,8 +306,8 @@ int dartray_dust_emission(dartray_grid *dust_grid, const dartray_grid *stellar_g
 int dartray_map_external(dartray_grid *grid, const double view[3], const double up[3], const double origin[2],
                          double pixel, int32_t nx, int32_t ny, int32_t use_jsca, float *map, int dst_is_device);
 
-/* Vector-Jacobian product of dartray_map_external, the radiation field of
- * the last sweep held fixed (the luminosity each crossing deposits into the
+/* Vector-Jacobian product of dartray_map_external (the map of Sect. 2,
+ * end), the radiation field of the last sweep held fixed (the luminosity each crossing deposits into the
  * scattering source function does not move):
  *   grad_kappa_rho[c][l] = sum over pixels of dmap[l][pixel]
  *                          d map[l][pixel] / d kappa_rho[c][l]
@@ -331,16 +334,19 @@ int dartray_map_external_vjp(dartray_grid *grid, const double view[3], const dou
  * outside the octant mode.  Errors: INVAL, CUDA. */
 int dartray_jsca_dg_arm(dartray_grid *grid, const double view[3]);
 
-/* The armed tally [n_leaf][n_lambda] (host or device).  Errors: INVAL,
- * STATE (not armed), CUDA. */
+/* The armed tally of d j_sca / d g (Eq. 4), [n_leaf][n_lambda] (host or
+ * device).  Errors: INVAL, STATE (not armed), CUDA. */
 int dartray_jsca_dg(dartray_grid *grid, float *out, int dst_is_device);
 
-/* Replace kappa_rho [n_leaf][n_lambda] (host or device), e.g. to map a
- * changed dust distribution; the RFED and j_sca keep their values until the
- * next sweep. */
+/* Replace kappa_rho [n_leaf][n_lambda] (host or device; the extinction per
+ * length of the problem's inputs, Sect. 2), e.g. to map a changed dust
+ * distribution; the RFED and j_sca keep their values until the next sweep.
+ * Errors: INVAL, CUDA. */
 int dartray_set_kappa_rho(dartray_grid *grid, const float *kappa_rho, int src_is_device);
 
-/* Replace the emissivity [n_leaf][n_lambda] (host or device). */
+/* Replace the emissivity [n_leaf][n_lambda] (host or device; the
+ * luminosity per volume per sr of the problem's inputs, Sect. 2; the dust
+ * emission of Sect. 3.3 goes in this way).  Errors: INVAL, CUDA. */
 int dartray_set_emissivity(dartray_grid *grid, const float *emissivity, int src_is_device);
 
 /* Step 2 for the current emissivity on top of the present state (Sect. 3.3,
@@ -352,7 +358,8 @@ int dartray_set_emissivity(dartray_grid *grid, const float *emissivity, int src_
 int dartray_direct_incremental(dartray_grid *grid, dartray_stats *stats);
 
 /* Autotuner: times steps 1 and 2 on every sample_stride-th source with each
- * deposit schedule -- 0: deferred per-cell records in the full buffer, 1:
+ * deposit schedule of the scattering source function (the per-record
+ * expansion follows the paper's communication mode, Sect. 3.4) -- 0: deferred per-cell records in the full buffer, 1:
  * deferred with a sixteenth of the buffer (smaller, more frequent flushes),
  * 2: per-pixel atomics in the ray marcher -- and keeps the fastest for the
  * later calls of the grid (results do not depend on the schedule).
@@ -363,23 +370,28 @@ int dartray_autotune(dartray_grid *grid, int32_t sample_stride, int32_t *choice,
 
 /* RFED U [n_leaf][n_lambda] and absorbed luminosity
  * L_abs = (1 - albedo) * kappa_rho * c_light * V * U [n_leaf][n_lambda]
- * (either pointer may be NULL), written to host or device memory. */
+ * (the outputs of Sect. 2; either pointer may be NULL), written to host or
+ * device memory.  Errors: INVAL, CUDA. */
 int dartray_rfed(dartray_grid *grid, float *U, float *L_abs, int dst_is_device);
 
-/* Forward mode (params.tangent_albedo): dU/d albedo [n_leaf][n_lambda] (the
+/* Forward mode (params.tangent_albedo; the deposits of Sect. 2
+ * differentiated with respect to the albedo): dU/d albedo [n_leaf][n_lambda] (the
  * derivative of each wavelength's U with respect to its own albedo, the
  * sweep's decisions held) and dL_abs/d albedo = kappa_rho c_light V
  * ((1 - albedo) dU - U), host or device memory (either may be NULL).
  * Errors: INVAL, STATE (not the forward mode), CUDA. */
 int dartray_rfed_tangent(dartray_grid *grid, float *dU, float *dL_abs, int dst_is_device);
 
-/* j_sca layout: k_lambda per wavelength, offset of each wavelength block and
- * total length; block l is [n_leaf][12 * 4^k_lambda[l]] (nested pixels). */
+/* j_sca layout: k_lambda per wavelength (Eq. 5), offset of each wavelength
+ * block and total length; block l is [n_leaf][12 * 4^k_lambda[l]] (nested
+ * HEALPix pixels, Sect. 3.1.2).  Errors: INVAL. */
 int dartray_jsca_layout(const dartray_grid *grid, int32_t *k_lambda, int64_t *offsets,
                         int64_t *total_len);
 
-/* Copy j_sca: which = 0 total scattered luminosity per pixel (all phases so
- * far), 1 = pending (deposited by the last phase).  out has total_len floats. */
+/* Copy j_sca, the scattering source function of Sect. 3.1.2 (Eq. 4): which
+ * = 0 total scattered luminosity per pixel (all phases so far), 1 = pending
+ * (deposited by the last phase).  out has total_len floats.  Errors: INVAL,
+ * CUDA. */
 int dartray_jsca(dartray_grid *grid, int which, float *out, int dst_is_device);
 
 /*
@@ -398,8 +410,8 @@ int dartray_map(dartray_grid *grid, const double observer[3], int32_t nside_k, i
                 int32_t use_jsca, float *map, int dst_is_device);
 
 /*
- * dartray_map without any device allocation, for callers that cannot call
- * cudaMalloc (for example code running under an allocator that forbids it,
+ * dartray_map (the internal-observer map of Sect. 3.6.3) without any device
+ * allocation, for callers that cannot call cudaMalloc (for example code running under an allocator that forbids it,
  * or an application that reserves all device memory up front).  The paper has
  * no counterpart; the result equals dartray_map's.
  *
@@ -418,7 +430,10 @@ int dartray_map_noalloc(dartray_grid *grid, const double observer[3], int32_t ns
 
 /* Save / restore the RFED and source-function state (U, U_LL, pending,
  * j_sca_total and the step-2 scattered luminosity) to a raw binary file, so
- * that maps can be made without repeating the sweep. */
+ * that maps can be made without repeating the sweep (the paper writes its
+ * outputs to HDF5 files, Sect. 3.6; this library keeps raw arrays).
+ * Errors: INVAL (batched grids, the forward mode, a file of another grid),
+ * CUDA. */
 int dartray_state_save(dartray_grid *grid, const char *path);
 int dartray_state_load(dartray_grid *grid, const char *path);
 
