@@ -136,3 +136,13 @@ def test_rfed_albedo_autograd_against_central_differences():
         fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
         print(f"d loss / d albedo[{l}]: autograd {float(alb.grad[l]):.6e}, central differences {fd:.6e}")
         assert abs(float(alb.grad[l]) - fd) <= REL_CELL * abs(fd)
+
+
+def test_tangent_three_wavelengths_padded():
+    """Three wavelengths in the forward mode: rays of 8 (3 wavelengths, one
+    padding, their 3 derivatives, one padding)."""
+    g1 = two_lambda_cube()
+    kr = g1.kappa_rho[:, :1] * np.array([1.0, 0.6, 0.3], np.float32)[None, :]
+    g = g1.with_lambda(kr, np.repeat(g1.emissivity[:, :1], 3, axis=1), [0.65, 0.55, 0.4], [0.7, 0.5, 0.3])
+    gpu, ref = run_pair(g, 1, a_rt=0.05, r_pre=0.5, tangent_albedo=1)
+    check_tangent(gpu, ref)
